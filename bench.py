@@ -1,0 +1,387 @@
+#!/usr/bin/env python
+"""Benchmark of the forward SU(2) FFT on one GB300 (and N GPUs as replicas).
+
+Workload (one step = one forward transform of the whole batch): bandwidth
+N = 256 Euler grid (256 alpha x 256 beta x 256 gamma), batch 64 functions,
+complex64, coefficients CN(0, (1+l)^-1) up to l = 127.5 drawn with seed 2
+(per rank r > 0: seed 2 + 1000 r), grids synthesised on the GPU by the
+library's own synthesis (su2_inverse) before timing.  Inputs (8.6 GB) are far
+larger than the 129 MB L2, so no explicit flush is needed between steps.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+instead (host cores, bounded sample per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SU(2) FFTs/s at N=256 batch 64: split-BF16 TC vs FP32 path, ≤1e-5 rel err"
+UNIT = "FFTs/s"
+WORKLOAD = ("forward SU(2) FFT, N=256 Euler grid (256^3 nodes), batch 64, complex64, "
+            "coefficients CN(0,(1+l)^-1) up to l=127.5, seed 2")
+SMS = 152
+FP32_LANES = 128
+
+
+def num_coeffs(N):
+    return N * (N + 1) * (2 * N + 1) // 6
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.dev)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+ORACLE_ROW_STRIDE = 16
+
+
+def oracle_sample_seconds(f64grid):
+    """Seconds for one oracle forward at this N, from a bounded sample.
+
+    Stage 1 (torus DFT, both sectors) runs in full; stage 2 runs for every
+    ORACLE_ROW_STRIDE-th n row and is scaled by the stride.
+    """
+    from oracle import grid as G, transform as T
+    N = f64grid.shape[0]
+    t0 = time.perf_counter()
+    al, ga = G.alpha_nodes(N), G.gamma_nodes(N)
+    for sector in ("int", "half"):
+        idx = T.sector_indices(N, sector)
+        T.torus_dft(f64grid, idx, idx, al, ga)
+    t1 = time.perf_counter()
+    T.forward_separable(f64grid, row_stride=ORACLE_ROW_STRIDE)
+    t2 = time.perf_counter()
+    stage1 = t1 - t0
+    stage2_sample = max((t2 - t1) - stage1, 0.0)
+    return stage1 + stage2_sample * ORACLE_ROW_STRIDE, (t2 - t0)
+
+
+def cpu_baseline_for(f64grid):
+    est, spent = oracle_sample_seconds(f64grid)
+    return {"value": 1.0 / est, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"one N={f64grid.shape[0]} function (function 0 of the batch): oracle stage 1 "
+                       f"(torus DFT, both sectors, numpy BLAS on up to {os.cpu_count()} threads) in full, "
+                       f"stage 2 (recurrence + theta contraction, single Python thread) on every "
+                       f"{ORACLE_ROW_STRIDE}th n row, scaled by {ORACLE_ROW_STRIDE}; {spent:.1f} s of CPU work"),
+            "seconds_per_fft": est}
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import su2inputs as I
+    N = args.N
+    rng = np.random.default_rng(2)
+    f = I.draw_grid_gaussian((N, N, N), rng).astype(np.complex64).astype(np.complex128)
+    times = []
+    for i in range(args.warmup + args.steps):
+        est, _ = oracle_sample_seconds(f)
+        if i >= args.warmup:
+            times.append(est)
+    per_fft = statistics.mean(times)
+    value = 1.0 / per_fft
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_fft * args.batch * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "N": N, "batch": args.batch},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": (f"per step: one N={N} function, oracle stage 1 in full, stage 2 on "
+                                        f"every {ORACLE_ROW_STRIDE}th n row scaled by {ORACLE_ROW_STRIDE}; "
+                                        f"value = FFTs/s of one host (the oracle is not batched)")},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU benchmark
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--algo", default="auto", choices=["auto", "fp32", "tc_bf16x3"])
+    ap.add_argument("--N", type=int, default=256)
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2605_23923_gb300 as su2
+    import su2inputs as I
+    from paper_2605_23923_gb300 import build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        dist.barrier()
+        build.build()
+
+    N, B = args.N, args.batch
+    algo = args.algo
+    if algo == "auto":
+        algo = "fp32"
+        try:
+            su2.Plan(N=N, batch=1, dtype="c64", algo="tc_bf16x3").close()
+            algo = "tc_bf16x3"
+        except su2.SU2Error:
+            pass
+    plan = su2.Plan(N=N, batch=B, dtype="c64", algo=algo)
+    stream = torch.cuda.current_stream()
+
+    # ---- inputs: seeded coefficients -> grids by the library's synthesis
+    C = num_coeffs(N)
+    rng = np.random.default_rng(2 + 1000 * rank)
+    coeffs = torch.empty(B * C, dtype=torch.complex64, device=dev)
+    for b in range(B):
+        c = I.draw_coeffs(N, rng, "inv1").astype(np.complex64)
+        coeffs[b * C:(b + 1) * C].copy_(torch.from_numpy(c))
+    grid = torch.empty(B * N ** 3, dtype=torch.complex64, device=dev)
+    syn = su2.Plan(N=N, batch=B, dtype="c64", algo="fp32")
+    syn.inverse(coeffs, out=grid, ws=plan.workspace())
+    syn.sync_status()
+    syn.close()
+    del coeffs
+    out = torch.empty(B * C, dtype=torch.complex64, device=dev)
+    ws = plan.workspace()
+
+    def step(ev=None):
+        if ev is None:
+            plan.forward_stage1(grid, ws=ws, stream=stream)
+            plan.forward_stage2(out=out, ws=ws, stream=stream)
+        else:
+            ev[0].record(stream)
+            plan.forward_stage1(grid, ws=ws, stream=stream)
+            ev[1].record(stream)
+            plan.forward_stage2(out=out, ws=ws, stream=stream)
+            ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    plan.sync_status()
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(args.steps):
+        step(evs[i])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    plan.sync_status()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    st1 = [e[0].elapsed_time(e[1]) for e in evs]
+    st2 = [e[1].elapsed_time(e[2]) for e in evs]
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    ms_per_step = elapsed_ms / args.steps
+    value = world * B * args.steps / (elapsed_ms / 1e3)
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        host_grid = torch.empty(B * N ** 3, dtype=torch.complex64, pin_memory=True)
+        host_grid.copy_(grid)
+        host_out = torch.empty(B * C, dtype=torch.complex64, pin_memory=True)
+        dgrid = torch.empty_like(grid)
+
+        def e2e_step():
+            dgrid.copy_(host_grid, non_blocking=True)
+            plan.forward(dgrid, out=out, ws=ws, stream=stream)
+            host_out.copy_(out, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        b_.record(stream)
+        torch.cuda.synchronize()
+        ems = a.elapsed_time(b_)
+        if world > 1:
+            t = torch.tensor([ems], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": world * B * args.e2e_steps / (ems / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": host_grid.numel() * 8, "d2h_bytes_per_step": host_out.numel() * 8,
+               "steps": args.e2e_steps}
+        del host_grid, host_out, dgrid
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel
+    peaks, peak_src = measured_peaks()
+    s1 = statistics.mean(st1) / 1e3
+    s2 = statistics.mean(st2) / 1e3
+    fft_bytes = B * (8 * N ** 3 + 8 * (2 * N * N - 2 * N + 1) * N)
+    fft_gbs = fft_bytes / s1 / 1e9
+    contr_flops = B * 4 * N * C
+    contr_bytes = B * (8 * (2 * N * N - 2 * N + 1) * N + 8 * C)
+    sm_mhz = clk["sm_mhz"] if clk else peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = SMS * FP32_LANES * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    stages = {
+        "stage1_fft": {"ms": s1 * 1e3, "GB/s": fft_gbs, "bound": "hbm",
+                       "frac": fft_gbs / peaks["hbm_gbs"], "alg_bytes": fft_bytes},
+        "stage2_contraction": {"ms": s2 * 1e3, "algo": algo, "alg_flops": contr_flops,
+                               "TFLOP/s": contr_flops / s2 / 1e12, "GB/s": contr_bytes / s2 / 1e9,
+                               "alg_bytes": contr_bytes},
+    }
+    if algo == "fp32":
+        stages["stage2_contraction"].update(bound="alu", peak_tflops=fp32_peak,
+                                            frac=contr_flops / s2 / 1e12 / fp32_peak)
+    else:
+        stages["stage2_contraction"].update(bound="hbm", frac=contr_bytes / s2 / 1e9 / peaks["hbm_gbs"])
+    if s1 >= s2:
+        roof = {"bound": "hbm", "achieved": fft_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": fft_gbs / peaks["hbm_gbs"], "traffic": None, "kernel": "stage-1 2-D DFT (fft_fwd_cluster)",
+                "peak_source": peak_src}
+    elif algo == "fp32":
+        ach = contr_flops / s2 / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
+                "traffic": None, "kernel": "stage-2 FP32 contraction (contract_fwd)",
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
+    else:
+        ach = contr_bytes / s2 / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": "stage-2 TC contraction",
+                "peak_source": peak_src}
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        f0 = grid[:N ** 3].cpu().numpy().astype(np.complex128).reshape(N, N, N)
+        cpu = cpu_baseline_for(f0)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if algo == "fp32" else "bf16x3/f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "batch": B, "algo": algo,
+                   "l2": "inputs larger than L2 (8.6 GB grids, 17 GB stage-1 planes per step)",
+                   "parallelism": f"replicas x{world} (no collective)"},
+        "roofline": roof,
+        "stages": stages,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,155 @@
+/*
+ * su2fft.h -- C ABI of the GB300 (sm_103a) Fourier transform on SU(2).
+ *
+ * The transform follows Delgado & Umana, "On The Fast Fourier Transform on
+ * SU(2)":
+ *
+ *   analysis (Sec. 3, Definition of the Fourier transform; Sec. 4, Euler-angle
+ *   integral with the normalised Haar measure 1/(8 pi^2)):
+ *       f^(l)_{mn} = <f, t^l_{nm}>,   t^l_{nm} = e^{-i(n alpha + m gamma)} P^l_{nm}(cos beta)
+ *   on the sampling grid of Sec. 4 (Definition of the sampling grid),
+ *       alpha_j = gamma_j = -pi + 2 pi j / N,  beta_k = k pi / (N - 1),  j, k = 0..N-1,
+ *   evaluated by the two-stage split of Sec. 4 (Proposition on the factorised
+ *   Riemann sum) and Sec. 6 (first- and second-stage Propositions, depth k = 1):
+ *     stage 1: for every beta_k a 2-D DFT over (alpha, gamma) -> f_2(beta_k; m, n);
+ *     stage 2: per (m, n) the beta contraction <s, P^l_{nm}> with the Wigner-d
+ *              values regenerated by their three-term recurrence in l (Sec. 4
+ *              Lemma for m = n = 0; Jacobi analogue for general m, n).
+ *   Discrete form computed (exactly, up to rounding):
+ *       f^(l)_{mn} = 1/(2N^2) sum_{j1,k,j2} w_k f[j1,k,j2] conj(t^l_{nm}(alpha_j1, beta_k, gamma_j2))
+ *   with w_k the Clenshaw-Curtis weights on x_k = cos(beta_k) (default) or the
+ *   paper-literal Riemann weights sin(beta_k) pi/(N-1).
+ *
+ *   synthesis (Sec. 3, Peter-Weyl expansion):
+ *       f = sum_l (2l+1) sum_{m,n} f^(l)_{mn} t^l_{nm}
+ *   backward (adjoint of the analysis map, used for gradients):
+ *       g_grid[j1,k,j2] = w_k/(2N^2) sum_{l,m,n} t^l_{nm}(j1,k,j2) g^(l)_{mn}
+ *
+ * Index domain (Sec. 3, Definition of t^l): l in {0, 1/2, 1, ...}, -l <= m, n <= l,
+ * l - m and l - n integers.  For bandwidth N the coefficients cover 2l = 0..N-1.
+ *
+ * Layouts (all complex numbers interleaved (re, im); c64 = 2 x float32,
+ * c128 = 2 x float64):
+ *   grid   : per function f[j1][k][j2], N^3 elements, j2 fastest;
+ *            function f starts at element su2_grid_offset(plan, f).
+ *   coeffs : per function, blocks j = 2l = 0..N-1; block j is the (j+1)x(j+1)
+ *            matrix f^(l) stored row-major with row m+l and column n+l, starting
+ *            at element j(j+1)(2j+1)/6; N(N+1)(2N+1)/6 elements per function;
+ *            function f starts at su2_coeff_offset(plan, f).
+ *
+ * Ownership: every pointer passed to su2_forward / su2_inverse / su2_backward
+ * is caller-owned DEVICE memory (the grid, the coefficients and the
+ * workspace), 16-byte aligned.  A plan owns only small device tables it
+ * allocates in su2_plan and frees in su2_destroy.  Execution calls allocate
+ * nothing, never modify their inputs, and are asynchronous on the given CUDA
+ * stream (NULL = legacy default stream).
+ *
+ * Errors: every call returns a su2_status; nothing throws across the ABI.
+ * Argument errors are detected on the host before any launch.  Device-side
+ * errors (a bounded wait that expired) are latched in a per-plan error word
+ * and reported by su2_sync_status.
+ */
+#ifndef SU2FFT_H
+#define SU2FFT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct su2_plan_s* su2_plan_t;
+
+typedef enum {
+    SU2_OK = 0,
+    SU2_ERR_INVALID_ARG = 1,   /* null pointer, bad enum, bad batch size    */
+    SU2_ERR_UNSUPPORTED = 2,   /* bandwidth or dtype/algo combination       */
+    SU2_ERR_OOM = 3,           /* plan-table allocation failed              */
+    SU2_ERR_CUDA = 4,          /* a CUDA runtime call failed                */
+    SU2_ERR_TIMEOUT = 5,       /* a device-side bounded wait expired        */
+    SU2_ERR_WORKSPACE = 6,     /* workspace pointer null while size > 0     */
+    SU2_ERR_ALIGNMENT = 7      /* a device pointer is not 16-byte aligned   */
+} su2_status;
+
+typedef enum { SU2_C64 = 0, SU2_C128 = 1 } su2_dtype;
+
+typedef enum {
+    SU2_ALGO_AUTO = 0,         /* FP64 for c128; FP32 for c64                     */
+    SU2_ALGO_FP64 = 1,         /* c128 only: FP64 DFT, FP64 recurrence/contraction */
+    SU2_ALGO_FP32 = 2,         /* c64: FP32 DFT, FP32 recurrence, FP32 FMA contraction */
+    SU2_ALGO_TC_BF16X3 = 3     /* c64: FP32 DFT, contraction on tensor cores with
+                                  split-BF16 operands (3 products), FP32 accumulate */
+} su2_algo;
+
+typedef enum {
+    SU2_WEIGHTS_CC = 0,        /* Clenshaw-Curtis on cos(beta_k): exact per sector */
+    SU2_WEIGHTS_RIEMANN = 1    /* paper-literal sin(beta_k) * pi/(N-1)            */
+} su2_weights;
+
+typedef struct {
+    int num_functions;   /* batch size, >= 1                                     */
+    const int* N;        /* host array [num_functions] of bandwidths, or NULL    */
+    int N_uniform;       /* bandwidth of every function when N == NULL           */
+    su2_dtype dtype;
+    su2_algo algo;
+    su2_weights weights;
+    unsigned flags;      /* reserved, must be 0                                   */
+    int device;          /* CUDA device ordinal the plan's tables live on        */
+} su2_plan_desc;
+
+/* Supported bandwidths: N a power of two with 4 <= N <= 512 (c64) and
+ * 4 <= N <= 256 (c128).  Anything else returns SU2_ERR_UNSUPPORTED. */
+
+/* Creates a plan: validates the descriptor, uploads the beta nodes, weights,
+ * half-angle logarithms, log-factorials and DFT twiddles for every distinct
+ * bandwidth.  *out is set only on SU2_OK. */
+su2_status su2_plan(su2_plan_t* out, const su2_plan_desc* desc);
+
+/* Bytes of device workspace that su2_forward / su2_inverse / su2_backward
+ * need (the stage-1 planes of every function: 2 N^3 complex each). */
+su2_status su2_workspace_size(su2_plan_t plan, size_t* bytes);
+
+/* Element offsets of function f inside the grid and coefficient buffers. */
+su2_status su2_grid_offset(su2_plan_t plan, int f, size_t* elems);
+su2_status su2_coeff_offset(su2_plan_t plan, int f, size_t* elems);
+/* Total elements of the grid and coefficient buffers for the whole batch. */
+su2_status su2_grid_elems(su2_plan_t plan, size_t* elems);
+su2_status su2_coeff_elems(su2_plan_t plan, size_t* elems);
+
+/* N(N+1)(2N+1)/6: coefficients of one function of bandwidth N (0 if N < 1). */
+size_t su2_num_coeffs(int N);
+
+/* Analysis: grid -> coeffs (Sec. 4 two-stage split).  ws: >= su2_workspace_size. */
+su2_status su2_forward(su2_plan_t plan, const void* grid, void* coeffs, void* ws,
+                       void* cuda_stream);
+
+/* The two stages of su2_forward, for callers that time or reuse them
+ * separately.  Stage 1 (Sec. 6 first-stage Proposition): grid -> stage-1 planes
+ * in ws (2-D DFT over alpha, gamma for every beta node, weights folded in).
+ * Stage 2 (Sec. 6 second-stage Proposition, depth 1): planes in ws -> coeffs
+ * (beta contraction with the Wigner-d recurrence fused in).  Running stage 1
+ * then stage 2 on the same stream is exactly su2_forward. */
+su2_status su2_forward_stage1(su2_plan_t plan, const void* grid, void* ws, void* cuda_stream);
+su2_status su2_forward_stage2(su2_plan_t plan, const void* ws, void* coeffs, void* cuda_stream);
+
+/* Synthesis: coeffs -> grid (Sec. 3 expansion with the (2l+1) factor). */
+su2_status su2_inverse(su2_plan_t plan, const void* coeffs, void* grid, void* ws,
+                       void* cuda_stream);
+
+/* Adjoint of su2_forward: grad_coeffs -> grad_grid (conjugate transpose of the
+ * analysis map; for a real loss this is the PyTorch gradient convention). */
+su2_status su2_backward(su2_plan_t plan, const void* grad_coeffs, void* grad_grid,
+                        void* ws, void* cuda_stream);
+
+/* Synchronises the stream and reports any latched device-side error; clears it. */
+su2_status su2_sync_status(su2_plan_t plan, void* cuda_stream);
+
+su2_status su2_destroy(su2_plan_t plan);
+
+const char* su2_status_string(su2_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SU2FFT_H */

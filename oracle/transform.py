@@ -131,12 +131,15 @@ def torus_dft(f: np.ndarray, nvals2: np.ndarray, mvals2: np.ndarray,
     return np.transpose(t, (1, 0, 2))
 
 
-def forward_separable(f: np.ndarray, weights: str = "cc", literal: bool = False) -> np.ndarray:
+def forward_separable(f: np.ndarray, weights: str = "cc", literal: bool = False,
+                      row_stride: int = 1) -> np.ndarray:
     """Forward transform by the two-stage separation (Sec. 4 and Sec. 6, k = 1).
 
     Stage 1: f_2(theta_k; m, n) by the torus double sum for every theta_k.
     Stage 2: f^(l)_{mn} = pref * sum_k w_k conj(P^l_{nm}(cos theta_k)) f_2(theta_k; m, n),
              conj(P^l_{nm}) = i^{n-m} d^l_{nm}.
+    row_stride > 1 runs stage 2 only for every row_stride-th n (a bounded
+    timing sample; the other coefficients stay zero).
     """
     N = f.shape[0]
     al, be, ga, w, pref = _setup(N, weights, literal)
@@ -146,6 +149,8 @@ def forward_separable(f: np.ndarray, weights: str = "cc", literal: bool = False)
         jtop = _top_j(N, sector)
         F2 = torus_dft(f, idx, idx, al, ga)            # [k, n, m]
         for ni, n2 in enumerate(idx):
+            if ni % row_stride:
+                continue
             for mi, m2 in enumerate(idx):
                 j0, D = basis.wigner_d_column(n2, m2, be, jtop)
                 if D.shape[0] == 0:

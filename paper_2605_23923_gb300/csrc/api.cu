@@ -1,0 +1,417 @@
+// C ABI of the SU(2) transform library (declared in include/su2fft.h).
+//
+// A plan groups the functions of a batch by bandwidth N and uploads, per
+// distinct N, the FP64 tables the kernels read: beta_k = k pi/(N-1) (Sec. 4
+// sampling grid), cos(beta_k) and its float hi/lo split, log2 cos(beta_k/2),
+// log2 sin(beta_k/2), the beta weights (Clenshaw-Curtis on cos(beta_k), or the
+// paper-literal sin(beta_k) pi/(N-1)), the DFT twiddles exp(2 pi i t/N) and
+// the half-bin twists exp(i pi t/N); plus log2(k!) for the recurrence seeds.
+// Execution calls launch, per group, stage 1 (2-D DFT per beta node) and
+// stage 2 (beta contraction with the recurrence fused in), asynchronously on
+// the caller's stream, allocating nothing.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "../../include/su2fft.h"
+#include "su2_internal.h"
+
+namespace {
+
+struct Band {
+    int N = 0;
+    std::vector<int> fids;
+    int* d_fidx = nullptr;
+    double* d_cosb = nullptr;
+    double* d_log2c = nullptr;
+    double* d_log2s = nullptr;
+    double* d_w64 = nullptr;
+    float* d_w32 = nullptr;
+    float2* d_xsplit = nullptr;
+    float2* d_om32 = nullptr;
+    double2* d_om64 = nullptr;
+    float2* d_twist32 = nullptr;
+    double2* d_twist64 = nullptr;
+};
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) return;
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) return;
+        ok = true;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+size_t ncoef(int N) { return N < 1 ? 0 : (size_t)N * (N + 1) * (2 * N + 1) / 6; }
+
+// Clenshaw-Curtis weights on x_k = cos(k pi/n), n = N-1: interpolate at the
+// nodes with sum'' a_j T_j (a_j = (2/n) sum''_k g_k cos(j k pi/n)) and
+// integrate termwise (int T_j = 2/(1-j^2), j even).
+void cc_weights(int N, std::vector<double>& w) {
+    const int n = N - 1;
+    w.assign(N, 0.0);
+    for (int k = 0; k < N; ++k) {
+        double s = 0.0;
+        for (int j = 0; j <= n; j += 2) {
+            const double hj = (j == 0 || j == n) ? 0.5 : 1.0;
+            s += hj * (2.0 / (1.0 - (double)j * j)) * cos((double)j * k * M_PI / n);
+        }
+        const double hk = (k == 0 || k == n) ? 0.5 : 1.0;
+        w[k] = (2.0 / n) * hk * s;
+    }
+}
+
+}  // namespace
+
+struct su2_plan_s {
+    int device = 0;
+    int B = 0;
+    su2_dtype dtype = SU2_C64;
+    su2_algo algo = SU2_ALGO_FP32;
+    su2_weights weights = SU2_WEIGHTS_CC;
+    std::vector<int> Ns;
+    std::vector<size_t> grid_off, coeff_off, ws_off;
+    size_t grid_total = 0, coeff_total = 0, ws_total = 0;
+    std::map<int, Band> bands;
+    std::vector<void*> allocs;
+    size_t* d_grid_off = nullptr;
+    size_t* d_coeff_off = nullptr;
+    size_t* d_ws_off = nullptr;
+    double* d_lf2 = nullptr;
+    int* d_err = nullptr;
+
+    template <typename T>
+    cudaError_t upload(T** dst, const T* src, size_t count) {
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+        if (e != cudaSuccess) return e;
+        allocs.push_back(p);
+        *dst = (T*)p;
+        return cudaMemcpy(p, src, count * sizeof(T), cudaMemcpyHostToDevice);
+    }
+    void release() {
+        for (void* p : allocs) cudaFree(p);
+        allocs.clear();
+    }
+};
+
+namespace {
+
+su2_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return SU2_OK;
+    if (e == cudaErrorMemoryAllocation) return SU2_ERR_OOM;
+    return SU2_ERR_CUDA;
+}
+
+cudaError_t build_band(su2_plan_s* P, Band& b) {
+    const int N = b.N;
+    std::vector<double> cosb(N), l2c(N), l2s(N), w;
+    std::vector<float> w32(N);
+    std::vector<float2> xs(N), om32(N), tw32(N);
+    std::vector<double2> om64(N), tw64(N);
+    for (int k = 0; k < N; ++k) {
+        const double beta = M_PI * k / (N - 1);
+        cosb[k] = cos(beta);
+        const double ch = cos(beta / 2), sh = sin(beta / 2);
+        l2c[k] = (k == N - 1) ? -INFINITY : log2(ch);
+        l2s[k] = (k == 0) ? -INFINITY : log2(sh);
+        const float hi = (float)cosb[k];
+        xs[k] = make_float2(hi, (float)(cosb[k] - (double)hi));
+    }
+    if (P->weights == SU2_WEIGHTS_CC) {
+        cc_weights(N, w);
+    } else {
+        w.resize(N);
+        for (int k = 0; k < N; ++k) w[k] = sin(M_PI * k / (N - 1)) * (M_PI / (N - 1));
+    }
+    for (int k = 0; k < N; ++k) w32[k] = (float)w[k];
+    for (int t = 0; t < N; ++t) {
+        const double a = 2.0 * M_PI * t / N, h = M_PI * t / N;
+        om64[t] = make_double2(cos(a), sin(a));
+        om32[t] = make_float2((float)cos(a), (float)sin(a));
+        tw64[t] = make_double2(cos(h), sin(h));
+        tw32[t] = make_float2((float)cos(h), (float)sin(h));
+    }
+    cudaError_t e;
+    if ((e = P->upload(&b.d_fidx, b.fids.data(), b.fids.size())) != cudaSuccess) return e;
+    if ((e = P->upload(&b.d_cosb, cosb.data(), N)) != cudaSuccess) return e;
+    if ((e = P->upload(&b.d_log2c, l2c.data(), N)) != cudaSuccess) return e;
+    if ((e = P->upload(&b.d_log2s, l2s.data(), N)) != cudaSuccess) return e;
+    if ((e = P->upload(&b.d_w64, w.data(), N)) != cudaSuccess) return e;
+    if ((e = P->upload(&b.d_w32, w32.data(), N)) != cudaSuccess) return e;
+    if ((e = P->upload(&b.d_xsplit, xs.data(), N)) != cudaSuccess) return e;
+    if ((e = P->upload(&b.d_om32, om32.data(), N)) != cudaSuccess) return e;
+    if ((e = P->upload(&b.d_om64, om64.data(), N)) != cudaSuccess) return e;
+    if ((e = P->upload(&b.d_twist32, tw32.data(), N)) != cudaSuccess) return e;
+    if ((e = P->upload(&b.d_twist64, tw64.data(), N)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+su2::BandArgs band_args(const su2_plan_s* P, const Band& b) {
+    su2::BandArgs a;
+    a.N = b.N;
+    a.nfunc = (int)b.fids.size();
+    a.fidx = b.d_fidx;
+    a.grid_off = P->d_grid_off;
+    a.coeff_off = P->d_coeff_off;
+    a.ws_off = P->d_ws_off;
+    a.cosb = b.d_cosb;
+    a.log2c = b.d_log2c;
+    a.log2s = b.d_log2s;
+    a.w64 = b.d_w64;
+    a.w32 = b.d_w32;
+    a.xsplit = b.d_xsplit;
+    a.lf2 = P->d_lf2;
+    a.om32 = b.d_om32;
+    a.om64 = b.d_om64;
+    a.twist32 = b.d_twist32;
+    a.twist64 = b.d_twist64;
+    a.err = P->d_err;
+    return a;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+su2_status check_exec(su2_plan_t plan, const void* in, const void* out, const void* ws) {
+    if (!plan || !in || !out) return SU2_ERR_INVALID_ARG;
+    if (plan->ws_total > 0 && !ws) return SU2_ERR_WORKSPACE;
+    if (!aligned16(in) || !aligned16(out) || (ws && !aligned16(ws))) return SU2_ERR_ALIGNMENT;
+    return SU2_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t su2_num_coeffs(int N) { return ncoef(N); }
+
+const char* su2_status_string(su2_status s) {
+    switch (s) {
+        case SU2_OK: return "ok";
+        case SU2_ERR_INVALID_ARG: return "invalid argument";
+        case SU2_ERR_UNSUPPORTED: return "unsupported bandwidth or dtype/algo combination";
+        case SU2_ERR_OOM: return "device allocation failed";
+        case SU2_ERR_CUDA: return "CUDA runtime error";
+        case SU2_ERR_TIMEOUT: return "device-side bounded wait expired";
+        case SU2_ERR_WORKSPACE: return "workspace missing";
+        case SU2_ERR_ALIGNMENT: return "device pointer not 16-byte aligned";
+    }
+    return "unknown status";
+}
+
+su2_status su2_plan(su2_plan_t* out, const su2_plan_desc* desc) {
+    if (!out || !desc) return SU2_ERR_INVALID_ARG;
+    if (desc->num_functions < 1 || desc->flags != 0) return SU2_ERR_INVALID_ARG;
+    if (desc->dtype != SU2_C64 && desc->dtype != SU2_C128) return SU2_ERR_INVALID_ARG;
+    if (desc->weights != SU2_WEIGHTS_CC && desc->weights != SU2_WEIGHTS_RIEMANN) return SU2_ERR_INVALID_ARG;
+    su2_algo algo = desc->algo;
+    if (algo == SU2_ALGO_AUTO) algo = (desc->dtype == SU2_C128) ? SU2_ALGO_FP64 : SU2_ALGO_FP32;
+    if (algo != SU2_ALGO_FP64 && algo != SU2_ALGO_FP32 && algo != SU2_ALGO_TC_BF16X3) return SU2_ERR_INVALID_ARG;
+    if ((algo == SU2_ALGO_FP64) != (desc->dtype == SU2_C128)) return SU2_ERR_UNSUPPORTED;
+    const int Nmax_allowed = (desc->dtype == SU2_C128) ? 256 : 512;
+    std::vector<int> Ns(desc->num_functions);
+    for (int f = 0; f < desc->num_functions; ++f) {
+        const int N = desc->N ? desc->N[f] : desc->N_uniform;
+        if (!is_pow2(N) || N < 4 || N > Nmax_allowed) return SU2_ERR_UNSUPPORTED;
+        if (algo == SU2_ALGO_TC_BF16X3 && !su2::tc_supported(N)) return SU2_ERR_UNSUPPORTED;
+        Ns[f] = N;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return SU2_ERR_CUDA;
+    if (desc->device < 0 || desc->device >= ndev) return SU2_ERR_INVALID_ARG;
+    DeviceGuard g(desc->device);
+    if (!g.ok) return SU2_ERR_CUDA;
+
+    su2_plan_s* P = new (std::nothrow) su2_plan_s();
+    if (!P) return SU2_ERR_OOM;
+    P->device = desc->device;
+    P->B = desc->num_functions;
+    P->dtype = desc->dtype;
+    P->algo = algo;
+    P->weights = desc->weights;
+    P->Ns = Ns;
+    P->grid_off.resize(P->B);
+    P->coeff_off.resize(P->B);
+    P->ws_off.resize(P->B);
+    int Nmax = 0;
+    for (int f = 0; f < P->B; ++f) {
+        const size_t N = (size_t)Ns[f];
+        P->grid_off[f] = P->grid_total;
+        P->coeff_off[f] = P->coeff_total;
+        P->ws_off[f] = P->ws_total;
+        P->grid_total += N * N * N;
+        P->coeff_total += ncoef((int)N);
+        P->ws_total += 2 * N * N * N;
+        P->bands[(int)N].fids.push_back(f);
+        Nmax = std::max(Nmax, (int)N);
+    }
+    std::vector<double> lf2(2 * Nmax + 2);
+    for (size_t k = 0; k < lf2.size(); ++k) lf2[k] = lgamma((double)k + 1.0) / log(2.0);
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = P->upload(&P->d_grid_off, P->grid_off.data(), P->B);
+    if (e == cudaSuccess) e = P->upload(&P->d_coeff_off, P->coeff_off.data(), P->B);
+    if (e == cudaSuccess) e = P->upload(&P->d_ws_off, P->ws_off.data(), P->B);
+    if (e == cudaSuccess) e = P->upload(&P->d_lf2, lf2.data(), lf2.size());
+    if (e == cudaSuccess) {
+        const int zero = 0;
+        e = P->upload(&P->d_err, &zero, 1);
+    }
+    for (auto& kv : P->bands) {
+        if (e != cudaSuccess) break;
+        kv.second.N = kv.first;
+        e = build_band(P, kv.second);
+    }
+    if (e != cudaSuccess) {
+        P->release();
+        delete P;
+        return from_cuda(e);
+    }
+    *out = P;
+    return SU2_OK;
+}
+
+su2_status su2_workspace_size(su2_plan_t plan, size_t* bytes) {
+    if (!plan || !bytes) return SU2_ERR_INVALID_ARG;
+    *bytes = plan->ws_total * (plan->dtype == SU2_C128 ? 16 : 8);
+    return SU2_OK;
+}
+
+su2_status su2_grid_offset(su2_plan_t plan, int f, size_t* elems) {
+    if (!plan || !elems || f < 0 || f >= plan->B) return SU2_ERR_INVALID_ARG;
+    *elems = plan->grid_off[f];
+    return SU2_OK;
+}
+
+su2_status su2_coeff_offset(su2_plan_t plan, int f, size_t* elems) {
+    if (!plan || !elems || f < 0 || f >= plan->B) return SU2_ERR_INVALID_ARG;
+    *elems = plan->coeff_off[f];
+    return SU2_OK;
+}
+
+su2_status su2_grid_elems(su2_plan_t plan, size_t* elems) {
+    if (!plan || !elems) return SU2_ERR_INVALID_ARG;
+    *elems = plan->grid_total;
+    return SU2_OK;
+}
+
+su2_status su2_coeff_elems(su2_plan_t plan, size_t* elems) {
+    if (!plan || !elems) return SU2_ERR_INVALID_ARG;
+    *elems = plan->coeff_total;
+    return SU2_OK;
+}
+
+su2_status su2_forward(su2_plan_t plan, const void* grid, void* coeffs, void* ws, void* stream) {
+    su2_status s = check_exec(plan, grid, coeffs, ws);
+    if (s != SU2_OK) return s;
+    DeviceGuard g(plan->device);
+    if (!g.ok) return SU2_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool fp64 = plan->dtype == SU2_C128;
+    for (auto& kv : plan->bands) {
+        const su2::BandArgs a = band_args(plan, kv.second);
+        cudaError_t e = su2::launch_fft_forward(a, fp64, grid, ws, st);
+        if (e == cudaSuccess) {
+            if (plan->algo == SU2_ALGO_TC_BF16X3) e = su2::launch_contract_forward_tc(a, ws, coeffs, st);
+            else e = su2::launch_contract_forward(a, fp64, ws, coeffs, st);
+        }
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    return SU2_OK;
+}
+
+su2_status su2_forward_stage1(su2_plan_t plan, const void* grid, void* ws, void* stream) {
+    su2_status s = check_exec(plan, grid, ws ? ws : grid, ws);
+    if (s != SU2_OK) return s;
+    DeviceGuard g(plan->device);
+    if (!g.ok) return SU2_ERR_CUDA;
+    const bool fp64 = plan->dtype == SU2_C128;
+    for (auto& kv : plan->bands) {
+        cudaError_t e = su2::launch_fft_forward(band_args(plan, kv.second), fp64, grid, ws, (cudaStream_t)stream);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    return SU2_OK;
+}
+
+su2_status su2_forward_stage2(su2_plan_t plan, const void* ws, void* coeffs, void* stream) {
+    su2_status s = check_exec(plan, ws ? ws : coeffs, coeffs, ws);
+    if (s != SU2_OK) return s;
+    DeviceGuard g(plan->device);
+    if (!g.ok) return SU2_ERR_CUDA;
+    const bool fp64 = plan->dtype == SU2_C128;
+    for (auto& kv : plan->bands) {
+        const su2::BandArgs a = band_args(plan, kv.second);
+        cudaError_t e = (plan->algo == SU2_ALGO_TC_BF16X3)
+                            ? su2::launch_contract_forward_tc(a, ws, coeffs, (cudaStream_t)stream)
+                            : su2::launch_contract_forward(a, fp64, ws, coeffs, (cudaStream_t)stream);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    return SU2_OK;
+}
+
+static su2_status run_transpose(su2_plan_t plan, su2::TransposeMode mode, const void* coeffs, void* grid,
+                                void* ws, void* stream) {
+    su2_status s = check_exec(plan, coeffs, grid, ws);
+    if (s != SU2_OK) return s;
+    DeviceGuard g(plan->device);
+    if (!g.ok) return SU2_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool fp64 = plan->dtype == SU2_C128;
+    for (auto& kv : plan->bands) {
+        const su2::BandArgs a = band_args(plan, kv.second);
+        cudaError_t e = su2::launch_contract_transpose(a, fp64, mode, coeffs, ws, st);
+        if (e == cudaSuccess) e = su2::launch_fft_inverse(a, fp64, ws, grid, st);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    return SU2_OK;
+}
+
+su2_status su2_inverse(su2_plan_t plan, const void* coeffs, void* grid, void* ws, void* stream) {
+    return run_transpose(plan, su2::TransposeMode::Synthesis, coeffs, grid, ws, stream);
+}
+
+su2_status su2_backward(su2_plan_t plan, const void* grad_coeffs, void* grad_grid, void* ws, void* stream) {
+    return run_transpose(plan, su2::TransposeMode::Adjoint, grad_coeffs, grad_grid, ws, stream);
+}
+
+su2_status su2_sync_status(su2_plan_t plan, void* stream) {
+    if (!plan) return SU2_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    if (!g.ok) return SU2_ERR_CUDA;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return SU2_ERR_CUDA;
+    int err = 0;
+    e = cudaMemcpy(&err, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return SU2_ERR_CUDA;
+    if (err != 0) {
+        const int zero = 0;
+        cudaMemcpy(plan->d_err, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        return SU2_ERR_TIMEOUT;
+    }
+    return SU2_OK;
+}
+
+su2_status su2_destroy(su2_plan_t plan) {
+    if (!plan) return SU2_ERR_INVALID_ARG;
+    {
+        DeviceGuard g(plan->device);
+        plan->release();
+    }
+    delete plan;
+    return SU2_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,235 @@
+// Device utilities shared by the SU(2) transform kernels: complex helpers,
+// compile-time-unrolled register DFTs, cluster shared-memory access and the
+// per-band argument structures.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace su2 {
+
+// ---------------------------------------------------------------------------
+// Complex numbers as (re, im) pairs of the working real type.
+// ---------------------------------------------------------------------------
+template <typename T> struct cplx_t;
+template <> struct cplx_t<float> { using type = float2; };
+template <> struct cplx_t<double> { using type = double2; };
+template <typename T> using cplx = typename cplx_t<T>::type;
+
+template <typename T> __device__ __forceinline__ cplx<T> mk(T r, T i) { cplx<T> z; z.x = r; z.y = i; return z; }
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { C z; z.x = a.x + b.x; z.y = a.y + b.y; return z; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { C z; z.x = a.x - b.x; z.y = a.y - b.y; return z; }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+    C z; z.x = a.x * b.x - a.y * b.y; z.y = a.x * b.y + a.y * b.x; return z;
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { C z; z.x = a.x; z.y = -a.y; return z; }
+template <typename C, typename T> __device__ __forceinline__ C cscale(C a, T s) { C z; z.x = a.x * s; z.y = a.y * s; return z; }
+// multiply by i^e (e taken mod 4)
+template <typename C> __device__ __forceinline__ C cmul_ipow(C a, int e) {
+    C z;
+    switch (e & 3) {
+        case 0: z = a; break;
+        case 1: z.x = -a.y; z.y = a.x; break;
+        case 2: z.x = -a.x; z.y = -a.y; break;
+        default: z.x = a.y; z.y = -a.x; break;
+    }
+    return z;
+}
+
+// cos and sin of 2*pi*t/32 for t = 0..31, constant-folded when t is known.
+template <typename T> __device__ __forceinline__ T tw32_cos(int t) {
+    switch (t & 31) {
+    case 0: return T(1);
+    case 1: return T(0.98078528040323043);
+    case 2: return T(0.92387953251128674);
+    case 3: return T(0.83146961230254524);
+    case 4: return T(0.70710678118654757);
+    case 5: return T(0.55557023301960229);
+    case 6: return T(0.38268343236508984);
+    case 7: return T(0.19509032201612833);
+    case 8: return T(0);
+    case 9: return T(-0.19509032201612819);
+    case 10: return T(-0.38268343236508973);
+    case 11: return T(-0.55557023301960196);
+    case 12: return T(-0.70710678118654746);
+    case 13: return T(-0.83146961230254535);
+    case 14: return T(-0.92387953251128674);
+    case 15: return T(-0.98078528040323043);
+    case 16: return T(-1);
+    case 17: return T(-0.98078528040323043);
+    case 18: return T(-0.92387953251128685);
+    case 19: return T(-0.83146961230254546);
+    case 20: return T(-0.70710678118654768);
+    case 21: return T(-0.55557023301960218);
+    case 22: return T(-0.38268343236509034);
+    case 23: return T(-0.19509032201612866);
+    case 24: return T(0);
+    case 25: return T(0.1950903220161283);
+    case 26: return T(0.38268343236509);
+    case 27: return T(0.55557023301960184);
+    case 28: return T(0.70710678118654735);
+    case 29: return T(0.83146961230254524);
+    case 30: return T(0.92387953251128652);
+    case 31: return T(0.98078528040323032);
+    }
+    return T(0);
+}
+template <typename T> __device__ __forceinline__ T tw32_sin(int t) {
+    switch (t & 31) {
+    case 0: return T(0);
+    case 1: return T(0.19509032201612825);
+    case 2: return T(0.38268343236508978);
+    case 3: return T(0.55557023301960218);
+    case 4: return T(0.70710678118654746);
+    case 5: return T(0.83146961230254524);
+    case 6: return T(0.92387953251128674);
+    case 7: return T(0.98078528040323043);
+    case 8: return T(1);
+    case 9: return T(0.98078528040323043);
+    case 10: return T(0.92387953251128674);
+    case 11: return T(0.83146961230254546);
+    case 12: return T(0.70710678118654757);
+    case 13: return T(0.55557023301960218);
+    case 14: return T(0.38268343236508989);
+    case 15: return T(0.19509032201612861);
+    case 16: return T(0);
+    case 17: return T(-0.19509032201612836);
+    case 18: return T(-0.38268343236508967);
+    case 19: return T(-0.55557023301960196);
+    case 20: return T(-0.70710678118654746);
+    case 21: return T(-0.83146961230254524);
+    case 22: return T(-0.92387953251128652);
+    case 23: return T(-0.98078528040323032);
+    case 24: return T(-1);
+    case 25: return T(-0.98078528040323043);
+    case 26: return T(-0.92387953251128663);
+    case 27: return T(-0.83146961230254546);
+    case 28: return T(-0.70710678118654768);
+    case 29: return T(-0.55557023301960218);
+    case 30: return T(-0.38268343236509039);
+    case 31: return T(-0.19509032201612872);
+    }
+    return T(0);
+}
+
+__host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n >> 1); }
+__host__ __device__ __forceinline__ constexpr int bitrev(int i, int bits) {
+    int r = 0;
+    for (int b = 0; b < bits; ++b) r = (r << 1) | ((i >> b) & 1);
+    return r;
+}
+
+// In-register DFT of length R (power of two, R <= 32):
+//   x[q] <- sum_j x[j] * exp(SIGN * 2 pi i q j / R).
+// Radix-2 decimation in time on a bit-reversed copy; the butterfly stages are
+// unrolled at compile time (template recursion over the stage length), so all
+// indices are constants and trivial twiddles (1, +-i) cost nothing.
+template <int R, int SIGN, typename T, int LEN>
+__device__ __forceinline__ void dft_stage(cplx<T> (&y)[R]) {
+    if constexpr (LEN <= R) {
+        constexpr int half = LEN / 2;
+        constexpr int step = 32 / LEN;           // omega_LEN^k = omega_32^(k * step)
+#pragma unroll
+        for (int i = 0; i < R; i += LEN) {
+#pragma unroll
+            for (int k = 0; k < half; ++k) {
+                const int t = k * step;
+                const cplx<T> b = y[i + k + half];
+                cplx<T> tb;
+                if (t == 0) {
+                    tb = b;
+                } else if (t == 8) {            // omega = SIGN * i
+                    tb = (SIGN > 0) ? mk<T>(-b.y, b.x) : mk<T>(b.y, -b.x);
+                } else {
+                    const T c = tw32_cos<T>(t);
+                    const T sn = (SIGN > 0) ? tw32_sin<T>(t) : -tw32_sin<T>(t);
+                    tb = mk<T>(b.x * c - b.y * sn, b.x * sn + b.y * c);
+                }
+                const cplx<T> a = y[i + k];
+                y[i + k] = cadd(a, tb);
+                y[i + k + half] = csub(a, tb);
+            }
+        }
+        dft_stage<R, SIGN, T, LEN * 2>(y);
+    }
+}
+
+template <int R, int SIGN, typename T>
+__device__ __forceinline__ void dft_reg(cplx<T> (&x)[R]) {
+    if constexpr (R > 1) {
+        constexpr int B = ilog2c(R);
+        cplx<T> y[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) y[i] = x[bitrev(i, B)];
+        dft_stage<R, SIGN, T, 2>(y);
+#pragma unroll
+        for (int i = 0; i < R; ++i) x[i] = y[i];
+    }
+}
+
+// Four-step split of a length-N DFT used by every transform kernel:
+// N = R1 * R2, pass A: R2-point DFTs over the stride-R1 subsequences,
+// pass B: R1-point DFTs over contiguous blocks.
+template <int N> struct Radix;
+template <> struct Radix<32>  { static constexpr int R1 = 8,  R2 = 4; };
+template <> struct Radix<64>  { static constexpr int R1 = 8,  R2 = 8; };
+template <> struct Radix<128> { static constexpr int R1 = 16, R2 = 8; };
+template <> struct Radix<256> { static constexpr int R1 = 16, R2 = 16; };
+template <> struct Radix<512> { static constexpr int R1 = 32, R2 = 16; };
+
+// ---------------------------------------------------------------------------
+// Thread-block cluster helpers (distributed shared memory).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned cluster_ctarank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Address of the same shared-memory location in CTA `rank` of this cluster.
+__device__ __forceinline__ uint32_t map_shared(const void* p, unsigned rank) {
+    uint32_t local = (uint32_t)__cvta_generic_to_shared(p);
+    uint32_t remote;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(rank));
+    return remote;
+}
+__device__ __forceinline__ float2 ld_dsmem(uint32_t addr, float2) {
+    float2 v;
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ double2 ld_dsmem(uint32_t addr, double2) {
+    double2 v;
+    asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(addr));
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// Arguments of one launch over a group of functions sharing the bandwidth N.
+// Element offsets are in complex elements.
+// ---------------------------------------------------------------------------
+struct BandArgs {
+    int N;
+    int nfunc;                    // functions in this launch group
+    const int* fidx;              // [nfunc] function ids
+    const size_t* grid_off;       // [num_functions] grid offsets
+    const size_t* coeff_off;      // [num_functions] coefficient offsets
+    const size_t* ws_off;         // [num_functions] stage-1 plane offsets
+    // per-band tables (device)
+    const double* cosb;           // cos(beta_k)
+    const double* log2c;          // log2 cos(beta_k/2)
+    const double* log2s;          // log2 sin(beta_k/2)
+    const double* w64;            // beta weights w_k
+    const float* w32;
+    const float2* xsplit;         // (hi, lo) float split of cos(beta_k)
+    const double* lf2;            // log2(k!) for k = 0..2N
+    const float2* om32;           // exp(+2 pi i t/N), t = 0..N-1
+    const double2* om64;
+    const float2* twist32;        // exp(+i pi t/N), t = 0..N-1
+    const double2* twist64;
+    int* err;                     // device error word
+};
+
+}  // namespace su2

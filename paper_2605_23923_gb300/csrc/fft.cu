@@ -1,0 +1,448 @@
+// Stage 1 of the SU(2) transform: the 2-D DFT over (alpha, gamma) for every
+// beta node (Sec. 4 factorised Riemann sum; Sec. 6 first-stage Proposition),
+// and its inverse for the synthesis / adjoint.
+//
+// Forward, for function f, node k and sector s (0: integer l, 1: half-integer l):
+//   F2_s[k][m][n] = w_k/(2N^2) (-1)^{n+m} sum_{j1,j2} f[j1,k,j2] tw_s(j1,j2) omega^{p j1 + q j2}
+//   omega = exp(+2 pi i/N), p = n mod N, q = m mod N (sector 0);
+//   sector 1 uses n = n0 + 1/2, m = m0 + 1/2, p = n0 mod N, q = m0 mod N and the
+//   pre-twist tw_1(j1,j2) = exp(i pi (j1 + j2)/N); tw_0 = 1.
+// This equals w_k/(2N^2) sum f exp(i(n alpha_j1 + m gamma_j2)) with
+// alpha_j = gamma_j = -pi + 2 pi j/N.  Storage: plane (k, s) of function f at
+// ws_off[f] + (2k + s) N^2, row mi = (q + N/2) mod N, column ni = (p + N/2) mod N
+// (n fastest).  In sector 0 row/column 0 (the Nyquist bin) is unused and
+// written as zero.
+//
+// Inverse: f[j1,k,j2] = sum_s conj(tw_s(j1,j2)) sum_{p,q} (-1)^{n+m} G_s[k][m][n] omega^{-(p j1 + q j2)}.
+//
+// Kernel design (N >= 32): one thread-block cluster of C = N/32 CTAs per plane;
+// CTA c holds the 32 columns j2 in [32c, 32c+32) of all N rows.  Pass 1 runs
+// the column DFTs over j1 (four-step: R2-point then R1-point register DFTs,
+// twiddle table in shared memory, padded [N][33] layout, lanes across columns).
+// After a cluster barrier, CTA c' gathers the rows p in [32c', 32c'+32) from
+// every CTA's shared memory (ld.shared::cluster) and runs the row DFTs over
+// j2; the second half of that DFT writes 32 consecutive n per warp store.
+#include "common.cuh"
+#include "su2_internal.h"
+
+namespace su2 {
+
+template <typename T> __device__ __forceinline__ cplx<T> om_at(const BandArgs& a, int t);
+template <> __device__ __forceinline__ float2 om_at<float>(const BandArgs& a, int t) { return a.om32[t]; }
+template <> __device__ __forceinline__ double2 om_at<double>(const BandArgs& a, int t) { return a.om64[t]; }
+template <typename T> __device__ __forceinline__ cplx<T> twist_at(const BandArgs& a, int t);
+template <> __device__ __forceinline__ float2 twist_at<float>(const BandArgs& a, int t) { return __ldg(a.twist32 + t); }
+template <> __device__ __forceinline__ double2 twist_at<double>(const BandArgs& a, int t) { return __ldg(a.twist64 + t); }
+template <typename T> __device__ __forceinline__ T weight_at(const BandArgs& a, int k);
+template <> __device__ __forceinline__ float weight_at<float>(const BandArgs& a, int k) { return a.w32[k]; }
+template <> __device__ __forceinline__ double weight_at<double>(const BandArgs& a, int k) { return a.w64[k]; }
+
+template <typename T, int N, int C>
+struct FftShape {
+    static constexpr int W = N / C;
+    static constexpr int R1 = Radix<N>::R1;
+    static constexpr int R2 = Radix<N>::R2;
+    static constexpr int LD1 = W + 1;
+    static constexpr int LD2 = N + 1;
+    static constexpr int BUF = (N * LD1 > W * LD2) ? N * LD1 : W * LD2;
+    static constexpr size_t smem_bytes() { return (size_t)(BUF + N) * sizeof(cplx<T>); }
+};
+
+// ---------------------------------------------------------------------------
+// Forward, cluster version
+// ---------------------------------------------------------------------------
+template <typename T, int N, int C, int THREADS>
+__global__ void __launch_bounds__(THREADS)
+fft_fwd_cluster(BandArgs a, const cplx<T>* __restrict__ grid, cplx<T>* __restrict__ ws) {
+    using Cx = cplx<T>;
+    using S = FftShape<T, N, C>;
+    constexpr int W = S::W, R1 = S::R1, R2 = S::R2, LD1 = S::LD1, LD2 = S::LD2;
+    static_assert(W == 32, "one warp of columns per CTA");
+    static_assert((W * R1) % THREADS == 0 && (W * R2) % THREADS == 0, "task split");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx* buf = reinterpret_cast<Cx*>(smem_raw);
+    Cx* om = buf + S::BUF;
+
+    const int c = (C > 1) ? (int)cluster_ctarank() : 0;
+    const int s = blockIdx.x / C;
+    const int k = blockIdx.y;
+    const int f = a.fidx[blockIdx.z];
+    const int tid = threadIdx.x;
+
+    for (int t = tid; t < N; t += THREADS) om[t] = om_at<T>(a, t);
+    __syncthreads();
+
+    const Cx* X = grid + a.grid_off[f] + (size_t)k * N;     // X[j1*N*N + j2]
+
+    // Pass 1A: column DFT, stride-R1 part, loaded straight from global memory.
+#pragma unroll
+    for (int it = 0; it < (W * R1) / THREADS; ++it) {
+        const int task = tid + it * THREADS;
+        const int jc = task % W, ia = task / W;
+        const int j2 = c * W + jc;
+        Cx v[R2];
+#pragma unroll
+        for (int b = 0; b < R2; ++b) v[b] = X[(size_t)(ia + R1 * b) * N * N + j2];
+        if (s) {
+            const Cx t2 = twist_at<T>(a, j2);
+#pragma unroll
+            for (int b = 0; b < R2; ++b) v[b] = cmul(v[b], cmul(twist_at<T>(a, ia + R1 * b), t2));
+        }
+        dft_reg<R2, 1, T>(v);
+#pragma unroll
+        for (int qb = 0; qb < R2; ++qb)
+            buf[(ia + R1 * qb) * LD1 + jc] = (qb == 0) ? v[0] : cmul(v[qb], om[ia * qb]);
+    }
+    __syncthreads();
+    // Pass 1B: contiguous R1-point DFTs; bin p = qb + R2*qa lands in row qa + R1*qb.
+#pragma unroll
+    for (int it = 0; it < (W * R2) / THREADS; ++it) {
+        const int task = tid + it * THREADS;
+        const int jc = task % W, qb = task / W;
+        Cx v[R1];
+#pragma unroll
+        for (int ia = 0; ia < R1; ++ia) v[ia] = buf[(ia + R1 * qb) * LD1 + jc];
+        dft_reg<R1, 1, T>(v);
+#pragma unroll
+        for (int qa = 0; qa < R1; ++qa) buf[(qa + R1 * qb) * LD1 + jc] = v[qa];
+    }
+    if constexpr (C > 1) cluster_sync_all(); else __syncthreads();
+
+    // Pass 2A: gather the owned rows p from all CTAs, stride-R1 part of the row DFT.
+    constexpr int NT2 = (W * R1) / THREADS;
+    Cx hold[NT2][R2];
+#pragma unroll
+    for (int it = 0; it < NT2; ++it) {
+        const int task = tid + it * THREADS;
+        const int pl = task % W, ia = task / W;
+        const int p = c * W + pl;
+        const int rowp = p / R2 + R1 * (p % R2);
+        Cx v[R2];
+#pragma unroll
+        for (int b = 0; b < R2; ++b) {
+            const int j2 = ia + R1 * b;
+            const Cx* src = &buf[rowp * LD1 + (j2 % W)];
+            if constexpr (C > 1) v[b] = ld_dsmem(map_shared(src, (unsigned)(j2 / W)), Cx());
+            else v[b] = *src;
+        }
+        dft_reg<R2, 1, T>(v);
+#pragma unroll
+        for (int qb = 0; qb < R2; ++qb) hold[it][qb] = (qb == 0) ? v[0] : cmul(v[qb], om[ia * qb]);
+    }
+    if constexpr (C > 1) cluster_sync_all(); else __syncthreads();
+#pragma unroll
+    for (int it = 0; it < NT2; ++it) {
+        const int task = tid + it * THREADS;
+        const int pl = task % W, ia = task / W;
+#pragma unroll
+        for (int qb = 0; qb < R2; ++qb) buf[pl * LD2 + ia + R1 * qb] = hold[it][qb];
+    }
+    __syncthreads();
+
+    // Pass 2B: R1-point DFTs, scale and store F2 rows (n fastest).
+    const T scale = weight_at<T>(a, k) / (T(2) * T(N) * T(N));
+    Cx* out = ws + a.ws_off[f] + ((size_t)k * 2 + s) * N * N;
+#pragma unroll
+    for (int it = 0; it < (W * R2) / THREADS; ++it) {
+        const int task = tid + it * THREADS;
+        const int pl = task % W, qb = task / W;
+        const int p = c * W + pl;
+        Cx v[R1];
+#pragma unroll
+        for (int ia = 0; ia < R1; ++ia) v[ia] = buf[pl * LD2 + ia + R1 * qb];
+        dft_reg<R1, 1, T>(v);
+        const int ni = (p + N / 2) & (N - 1);
+#pragma unroll
+        for (int qa = 0; qa < R1; ++qa) {
+            const int q = qb + R2 * qa;
+            const int mi = (q + N / 2) & (N - 1);
+            T sg = ((ni + mi) & 1) ? T(-1) : T(1);
+            if (s) sg = -sg;
+            Cx val = cscale(v[qa], sg * scale);
+            if (s == 0 && (ni == 0 || mi == 0)) val = mk<T>(T(0), T(0));
+            out[(size_t)mi * N + ni] = val;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Inverse, cluster version.  CTA c owns the n-bins p in [32c, 32c+32) for pass 1
+// and the output columns j2 in [32c, 32c+32) for pass 2; both sectors are
+// accumulated in registers before the single store.
+// ---------------------------------------------------------------------------
+template <typename T, int N, int C, int THREADS>
+__global__ void __launch_bounds__(THREADS)
+fft_inv_cluster(BandArgs a, const cplx<T>* __restrict__ ws, cplx<T>* __restrict__ grid) {
+    using Cx = cplx<T>;
+    using S = FftShape<T, N, C>;
+    constexpr int W = S::W, R1 = S::R1, R2 = S::R2, LD1 = S::LD1, LD2 = S::LD2;
+    static_assert(W == 32, "one warp of columns per CTA");
+    static_assert((W * R1) % THREADS == 0 && (W * R2) % THREADS == 0, "task split");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx* buf = reinterpret_cast<Cx*>(smem_raw);
+    Cx* om = buf + S::BUF;
+
+    const int c = (C > 1) ? (int)cluster_ctarank() : 0;
+    const int k = blockIdx.y;
+    const int f = a.fidx[blockIdx.z];
+    const int tid = threadIdx.x;
+
+    for (int t = tid; t < N; t += THREADS) om[t] = cconj(om_at<T>(a, t));   // exp(-2 pi i t/N)
+    __syncthreads();
+
+    constexpr int NTB = (W * R2) / THREADS;
+    Cx acc[NTB][R1];
+
+    for (int s = 0; s < 2; ++s) {
+        const Cx* G = ws + a.ws_off[f] + ((size_t)k * 2 + s) * N * N;   // [mi][ni]
+        // Pass 1A: DFT over q (rows of G) for the owned columns p.
+#pragma unroll
+        for (int it = 0; it < (W * R1) / THREADS; ++it) {
+            const int task = tid + it * THREADS;
+            const int pl = task % W, ia = task / W;
+            const int p = c * W + pl;
+            const int ni = (p + N / 2) & (N - 1);
+            Cx v[R2];
+#pragma unroll
+            for (int b = 0; b < R2; ++b) {
+                const int q = ia + R1 * b;
+                const int mi = (q + N / 2) & (N - 1);
+                T sg = ((ni + mi) & 1) ? T(-1) : T(1);
+                if (s) sg = -sg;
+                v[b] = (s == 0 && (ni == 0 || mi == 0)) ? mk<T>(T(0), T(0))
+                                                        : cscale(G[(size_t)mi * N + ni], sg);
+            }
+            dft_reg<R2, -1, T>(v);
+#pragma unroll
+            for (int qb = 0; qb < R2; ++qb)
+                buf[(ia + R1 * qb) * LD1 + pl] = (qb == 0) ? v[0] : cmul(v[qb], om[ia * qb]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int it = 0; it < (W * R2) / THREADS; ++it) {
+            const int task = tid + it * THREADS;
+            const int pl = task % W, qb = task / W;
+            Cx v[R1];
+#pragma unroll
+            for (int ia = 0; ia < R1; ++ia) v[ia] = buf[(ia + R1 * qb) * LD1 + pl];
+            dft_reg<R1, -1, T>(v);
+#pragma unroll
+            for (int qa = 0; qa < R1; ++qa) buf[(qa + R1 * qb) * LD1 + pl] = v[qa];
+        }
+        if constexpr (C > 1) cluster_sync_all(); else __syncthreads();
+
+        // Pass 2A: gather, for the owned output columns j2, all p from every CTA.
+        constexpr int NT2 = (W * R1) / THREADS;
+        Cx hold[NT2][R2];
+#pragma unroll
+        for (int it = 0; it < NT2; ++it) {
+            const int task = tid + it * THREADS;
+            const int jl = task % W, ia = task / W;
+            const int j2 = c * W + jl;
+            const int rowj = j2 / R2 + R1 * (j2 % R2);
+            Cx v[R2];
+#pragma unroll
+            for (int b = 0; b < R2; ++b) {
+                const int p = ia + R1 * b;
+                const Cx* src = &buf[rowj * LD1 + (p % W)];
+                if constexpr (C > 1) v[b] = ld_dsmem(map_shared(src, (unsigned)(p / W)), Cx());
+                else v[b] = *src;
+            }
+            dft_reg<R2, -1, T>(v);
+#pragma unroll
+            for (int qb = 0; qb < R2; ++qb) hold[it][qb] = (qb == 0) ? v[0] : cmul(v[qb], om[ia * qb]);
+        }
+        if constexpr (C > 1) cluster_sync_all(); else __syncthreads();
+#pragma unroll
+        for (int it = 0; it < NT2; ++it) {
+            const int task = tid + it * THREADS;
+            const int jl = task % W, ia = task / W;
+#pragma unroll
+            for (int qb = 0; qb < R2; ++qb) buf[jl * LD2 + ia + R1 * qb] = hold[it][qb];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int it = 0; it < NTB; ++it) {
+            const int task = tid + it * THREADS;
+            const int jl = task % W, qb = task / W;
+            const int j2 = c * W + jl;
+            Cx v[R1];
+#pragma unroll
+            for (int ia = 0; ia < R1; ++ia) v[ia] = buf[jl * LD2 + ia + R1 * qb];
+            dft_reg<R1, -1, T>(v);
+#pragma unroll
+            for (int qa = 0; qa < R1; ++qa) {
+                Cx val = v[qa];
+                if (s) {
+                    const int j1 = qb + R2 * qa;
+                    val = cmul(val, cconj(cmul(twist_at<T>(a, j1), twist_at<T>(a, j2))));
+                    acc[it][qa] = cadd(acc[it][qa], val);
+                } else {
+                    acc[it][qa] = val;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    Cx* Y = grid + a.grid_off[f] + (size_t)k * N;
+#pragma unroll
+    for (int it = 0; it < NTB; ++it) {
+        const int task = tid + it * THREADS;
+        const int jl = task % W, qb = task / W;
+        const int j2 = c * W + jl;
+#pragma unroll
+        for (int qa = 0; qa < R1; ++qa) {
+            const int j1 = qb + R2 * qa;
+            Y[(size_t)j1 * N * N + j2] = acc[it][qa];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Small bandwidths (N <= 16): one CTA per plane, direct DFT sums in shared memory.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+fft_fwd_small(BandArgs a, const cplx<T>* __restrict__ grid, cplx<T>* __restrict__ ws) {
+    using Cx = cplx<T>;
+    __shared__ Cx x[16 * 16], y[16 * 16], om[16];
+    const int N = a.N;
+    const int s = blockIdx.x, k = blockIdx.y, f = a.fidx[blockIdx.z];
+    const int tid = threadIdx.x;
+    if (tid < N) om[tid] = om_at<T>(a, tid);
+    const Cx* X = grid + a.grid_off[f] + (size_t)k * N;
+    for (int e = tid; e < N * N; e += blockDim.x) {
+        const int j1 = e / N, j2 = e % N;
+        Cx v = X[(size_t)j1 * N * N + j2];
+        if (s) v = cmul(v, cmul(twist_at<T>(a, j1), twist_at<T>(a, j2)));
+        x[e] = v;
+    }
+    __syncthreads();
+    for (int e = tid; e < N * N; e += blockDim.x) {        // y[j1][q] = sum_j2 x omega^{q j2}
+        const int j1 = e / N, q = e % N;
+        Cx acc = mk<T>(T(0), T(0));
+        for (int j2 = 0; j2 < N; ++j2) acc = cadd(acc, cmul(x[j1 * N + j2], om[(q * j2) % N]));
+        y[e] = acc;
+    }
+    __syncthreads();
+    const T scale = weight_at<T>(a, k) / (T(2) * T(N) * T(N));
+    Cx* out = ws + a.ws_off[f] + ((size_t)k * 2 + s) * N * N;
+    for (int e = tid; e < N * N; e += blockDim.x) {        // z[p][q] = sum_j1 y omega^{p j1}
+        const int q = e / N, p = e % N;
+        Cx acc = mk<T>(T(0), T(0));
+        for (int j1 = 0; j1 < N; ++j1) acc = cadd(acc, cmul(y[j1 * N + q], om[(p * j1) % N]));
+        const int ni = (p + N / 2) % N, mi = (q + N / 2) % N;
+        T sg = ((ni + mi) & 1) ? T(-1) : T(1);
+        if (s) sg = -sg;
+        Cx val = cscale(acc, sg * scale);
+        if (s == 0 && (ni == 0 || mi == 0)) val = mk<T>(T(0), T(0));
+        out[(size_t)mi * N + ni] = val;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+fft_inv_small(BandArgs a, const cplx<T>* __restrict__ ws, cplx<T>* __restrict__ grid) {
+    using Cx = cplx<T>;
+    __shared__ Cx x[16 * 16], y[16 * 16], om[16];
+    const int N = a.N;
+    const int k = blockIdx.y, f = a.fidx[blockIdx.z];
+    const int tid = threadIdx.x;
+    if (tid < N) om[tid] = cconj(om_at<T>(a, tid));
+    Cx acc2[1];
+    const int nE = N * N;
+    // each thread owns output elements e = tid (N*N <= 256)
+    acc2[0] = mk<T>(T(0), T(0));
+    for (int s = 0; s < 2; ++s) {
+        const Cx* G = ws + a.ws_off[f] + ((size_t)k * 2 + s) * N * N;
+        __syncthreads();
+        for (int e = tid; e < nE; e += blockDim.x) {      // x[q][p] = signed G
+            const int q = e / N, p = e % N;
+            const int ni = (p + N / 2) % N, mi = (q + N / 2) % N;
+            T sg = ((ni + mi) & 1) ? T(-1) : T(1);
+            if (s) sg = -sg;
+            x[e] = (s == 0 && (ni == 0 || mi == 0)) ? mk<T>(T(0), T(0))
+                                                    : cscale(G[(size_t)mi * N + ni], sg);
+        }
+        __syncthreads();
+        for (int e = tid; e < nE; e += blockDim.x) {      // y[j2][p] = sum_q x[q][p] om^{q j2}
+            const int j2 = e / N, p = e % N;
+            Cx acc = mk<T>(T(0), T(0));
+            for (int q = 0; q < N; ++q) acc = cadd(acc, cmul(x[q * N + p], om[(q * j2) % N]));
+            y[e] = acc;
+        }
+        __syncthreads();
+        if (tid < nE) {
+            const int j1 = tid / N, j2 = tid % N;
+            Cx acc = mk<T>(T(0), T(0));
+            for (int p = 0; p < N; ++p) acc = cadd(acc, cmul(y[j2 * N + p], om[(p * j1) % N]));
+            if (s) acc = cmul(acc, cconj(cmul(twist_at<T>(a, j1), twist_at<T>(a, j2))));
+            acc2[0] = cadd(acc2[0], acc);
+        }
+    }
+    if (tid < nE) {
+        const int j1 = tid / N, j2 = tid % N;
+        grid[a.grid_off[f] + ((size_t)j1 * N + k) * N + j2] = acc2[0];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+template <typename T, int N, int C, int THREADS, bool FWD>
+static cudaError_t launch_cluster(const BandArgs& a, const void* in, void* out, cudaStream_t st) {
+    using S = FftShape<T, N, C>;
+    auto kern = FWD ? (void (*)(BandArgs, const cplx<T>*, cplx<T>*))fft_fwd_cluster<T, N, C, THREADS>
+                    : (void (*)(BandArgs, const cplx<T>*, cplx<T>*))fft_inv_cluster<T, N, C, THREADS>;
+    const size_t smem = S::smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (C > 8) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(FWD ? 2 * C : C, N, a.nfunc);
+    cfg.blockDim = dim3(THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, a, (const cplx<T>*)in, (cplx<T>*)out);
+}
+
+template <typename T, bool FWD>
+static cudaError_t launch_any(const BandArgs& a, const void* in, void* out, cudaStream_t st) {
+    if (a.nfunc <= 0) return cudaSuccess;
+    switch (a.N) {
+        case 4: case 8: case 16: {
+            dim3 g(FWD ? 2 : 1, a.N, a.nfunc);
+            if (FWD) fft_fwd_small<T><<<g, 256, 0, st>>>(a, (const cplx<T>*)in, (cplx<T>*)out);
+            else fft_inv_small<T><<<g, 256, 0, st>>>(a, (const cplx<T>*)in, (cplx<T>*)out);
+            return cudaGetLastError();
+        }
+        case 32: return launch_cluster<T, 32, 1, 128, FWD>(a, in, out, st);
+        case 64: return launch_cluster<T, 64, 2, 256, FWD>(a, in, out, st);
+        case 128: return launch_cluster<T, 128, 4, 256, FWD>(a, in, out, st);
+        case 256: return launch_cluster<T, 256, 8, 256, FWD>(a, in, out, st);
+        case 512:
+            if constexpr (sizeof(T) == 4) return launch_cluster<T, 512, 16, 512, FWD>(a, in, out, st);
+            else return cudaErrorInvalidValue;
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_fft_forward(const BandArgs& a, bool fp64, const void* grid, void* ws, cudaStream_t st) {
+    return fp64 ? launch_any<double, true>(a, grid, ws, st) : launch_any<float, true>(a, grid, ws, st);
+}
+
+cudaError_t launch_fft_inverse(const BandArgs& a, bool fp64, const void* ws, void* grid, cudaStream_t st) {
+    return fp64 ? launch_any<double, false>(a, ws, grid, st) : launch_any<float, false>(a, ws, grid, st);
+}
+
+}  // namespace su2

@@ -1,0 +1,27 @@
+// Internal declarations shared by the C-ABI implementation and the kernel files.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace su2 {
+
+// Stage 1: 2-D DFT over (alpha, gamma) for every beta node (forward), and the
+// inverse torus synthesis.  `fp64` selects complex128 data.
+cudaError_t launch_fft_forward(const BandArgs& a, bool fp64, const void* grid, void* ws, cudaStream_t st);
+cudaError_t launch_fft_inverse(const BandArgs& a, bool fp64, const void* ws, void* grid, cudaStream_t st);
+
+// Stage 2: beta contraction with the recurrence fused in (forward), and the
+// transposed contraction (synthesis with weight 2l+1, or adjoint with weight
+// w_k/(2N^2)).
+cudaError_t launch_contract_forward(const BandArgs& a, bool fp64, const void* ws, void* coeffs, cudaStream_t st);
+enum class TransposeMode { Synthesis = 0, Adjoint = 1 };
+cudaError_t launch_contract_transpose(const BandArgs& a, bool fp64, TransposeMode mode, const void* coeffs,
+                                      void* ws, cudaStream_t st);
+
+// Stage 2 on tensor cores (split-BF16 operands, FP32 accumulation).
+cudaError_t launch_contract_forward_tc(const BandArgs& a, const void* ws, void* coeffs, cudaStream_t st);
+bool tc_supported(int N);
+
+}  // namespace su2

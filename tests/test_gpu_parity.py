@@ -1,0 +1,220 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Inputs are seeded (su2inputs) and, where band-limited, synthesised by the
+oracle in FP64; the grid is cast to the GPU dtype first and the oracle
+analyses the same cast values.  Error metric: max |gpu - oracle| over all
+coefficients of a function divided by max |oracle| (then max over the batch).
+Tolerances: 1e-12 for the FP64 path, 1e-5 for the FP32 path.
+"""
+import numpy as np
+import pytest
+
+import su2inputs as I
+from oracle import transform as T
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def su2():
+    import paper_2605_23923_gb300 as m
+    from paper_2605_23923_gb300 import build
+    build.build()
+    return m
+
+
+def rel(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / np.max(np.abs(np.asarray(b))))
+
+
+def cast(x, dtype):
+    return x.astype(np.complex64).astype(np.complex128) if dtype == "c64" else x.astype(np.complex128)
+
+
+def to_dev(x, dtype):
+    t = torch.from_numpy(np.ascontiguousarray(x.astype(np.complex64 if dtype == "c64" else np.complex128)))
+    return t.reshape(-1).cuda()
+
+
+def tol(dtype):
+    return TOL64 if dtype == "c128" else TOL32
+
+
+def run_forward(su2, grids, dtype, Ns=None, weights="cc", algo="auto"):
+    if Ns is None:
+        plan = su2.Plan(N=grids[0].shape[0], batch=len(grids), dtype=dtype, weights=weights, algo=algo)
+    else:
+        plan = su2.Plan(Ns=Ns, dtype=dtype, weights=weights, algo=algo)
+    flat = np.concatenate([g.reshape(-1) for g in grids])
+    out = plan.forward(to_dev(flat, dtype))
+    plan.sync_status()
+    out = out.cpu().numpy().astype(np.complex128)
+    return plan, [out[o:o + I.num_coeffs(n)] for o, n in zip(plan.coeff_offsets, plan.Ns)]
+
+
+# ---------------------------------------------------------------------------
+# Forward
+# ---------------------------------------------------------------------------
+
+def test_config1_fp64_n16_vs_direct(su2):
+    """N = 16, complex128, coefficients CN(0,1) seed 0, against the direct O(N^6) sum."""
+    N = 16
+    c = I.draw_coeffs(N, np.random.default_rng(0), "flat")
+    f = T.inverse_separable(c, N)
+    ref = T.forward_direct(f)
+    _, (got,) = run_forward(su2, [f], "c128")
+    assert rel(got, ref) < TOL64
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("N", [4, 8, 16, 32, 64])
+def test_forward_random_grid(su2, N, dtype):
+    f = cast(I.draw_grid_gaussian((N, N, N), np.random.default_rng(1000 + N)), dtype)
+    ref = T.forward_separable(f)
+    _, (got,) = run_forward(su2, [f], dtype)
+    assert rel(got, ref) < tol(dtype), rel(got, ref)
+
+
+@pytest.mark.parametrize("dtype", ["c64"])
+def test_forward_n128_bandlimited(su2, dtype):
+    N = 128
+    rng = np.random.default_rng(77)
+    f = cast(I.draw_grid_gaussian((N, N, N), rng), dtype)
+    # sampled pairs (the full O(N^4) oracle is slow at N = 128)
+    _, (got,) = run_forward(su2, [f], dtype)
+    from oracle import grid as G
+    worst, scale = 0.0, 0.0
+    pairs = [(0, 0), (126, 126), (-126, 126), (127, -127), (1, 1), (-37, 64), (50, -3), (-99, -99)]
+    for n2, m2 in pairs:
+        j0, vals = T.forward_pair(f, n2, m2)
+        for i, v in enumerate(vals):
+            worst = max(worst, abs(got[G.coeff_index(j0 + 2 * i, m2, n2)] - v))
+            scale = max(scale, abs(v))
+    assert worst / scale < TOL32
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_forward_batch(su2, dtype):
+    N, B = 32, 3
+    rng = np.random.default_rng(5)
+    grids = [cast(I.draw_grid_gaussian((N, N, N), rng), dtype) for _ in range(B)]
+    _, outs = run_forward(su2, grids, dtype)
+    for g, o in zip(grids, outs):
+        assert rel(o, T.forward_separable(g)) < tol(dtype)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_forward_ragged(su2, dtype):
+    Ns = [16, 64, 4, 32, 16, 8]
+    rng = np.random.default_rng(6)
+    grids = [cast(I.draw_grid_gaussian((n, n, n), rng), dtype) for n in Ns]
+    _, outs = run_forward(su2, grids, dtype, Ns=Ns)
+    for g, o in zip(grids, outs):
+        assert rel(o, T.forward_separable(g)) < tol(dtype)
+
+
+def test_forward_riemann_weights(su2):
+    N = 16
+    f = I.draw_grid_gaussian((N, N, N), np.random.default_rng(8))
+    _, (got,) = run_forward(su2, [f], "c128", weights="riemann")
+    assert rel(got, T.forward_separable(f, weights="riemann")) < TOL64
+
+
+def test_constant_function(su2):
+    N = 32
+    f = np.ones((N, N, N), dtype=np.complex128)
+    _, (got,) = run_forward(su2, [f], "c64")
+    ref = T.forward_separable(f)
+    assert abs(got[0] - 1.0) < 1e-6
+    assert rel(got, ref) < TOL32
+
+
+def test_config2_forward_and_inverse_n64(su2):
+    """N = 64 complex64: coefficients CN(0,(1+l)^-2) seed 1, plus N(0, 0.01) grid noise."""
+    N = 64
+    rng = np.random.default_rng(1)
+    c = I.draw_coeffs(N, rng, "inv2")
+    f = T.inverse_separable(c, N) + I.draw_grid_noise((N, N, N), 0.01, rng)
+    f = cast(f, "c64")
+    plan, (got,) = run_forward(su2, [f], "c64")
+    assert rel(got, T.forward_separable(f)) < TOL32
+    # inverse of the (cast) coefficients
+    c32 = cast(c, "c64")
+    g = plan.inverse(to_dev(c32, "c64"))
+    plan.sync_status()
+    g = g.cpu().numpy().astype(np.complex128).reshape(N, N, N)
+    assert rel(g, T.inverse_separable(c32, N)) < TOL32
+
+
+# ---------------------------------------------------------------------------
+# Inverse and adjoint
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("N", [4, 16, 32, 64])
+def test_inverse(su2, N, dtype):
+    c = cast(I.draw_coeffs(N, np.random.default_rng(200 + N)), dtype)
+    plan = su2.Plan(N=N, batch=1, dtype=dtype)
+    g = plan.inverse(to_dev(c, dtype))
+    plan.sync_status()
+    g = g.cpu().numpy().astype(np.complex128).reshape(N, N, N)
+    assert rel(g, T.inverse_separable(c, N)) < tol(dtype)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("N", [8, 32, 64])
+def test_adjoint(su2, N, dtype):
+    c = cast(I.draw_coeffs(N, np.random.default_rng(300 + N)), dtype)
+    plan = su2.Plan(N=N, batch=1, dtype=dtype)
+    g = plan.backward(to_dev(c, dtype))
+    plan.sync_status()
+    g = g.cpu().numpy().astype(np.complex128).reshape(N, N, N)
+    assert rel(g, T.adjoint_separable(c, N)) < tol(dtype)
+
+
+def test_inverse_ragged(su2):
+    Ns = [32, 8, 16]
+    rng = np.random.default_rng(9)
+    cs = [cast(I.draw_coeffs(n, rng), "c64") for n in Ns]
+    plan = su2.Plan(Ns=Ns, dtype="c64")
+    g = plan.inverse(to_dev(np.concatenate(cs), "c64"))
+    plan.sync_status()
+    g = g.cpu().numpy().astype(np.complex128)
+    for n, c, o in zip(Ns, cs, plan.grid_offsets):
+        assert rel(g[o:o + n ** 3].reshape(n, n, n), T.inverse_separable(c, n)) < TOL32
+
+
+def test_roundtrip_sector_fp64(su2):
+    N = 32
+    c = I.draw_coeffs(N, np.random.default_rng(10))
+    two_l = I.packed_two_l(N)
+    cs = np.where(two_l % 2 == 0, c, 0)
+    plan = su2.Plan(N=N, batch=1, dtype="c128")
+    back = plan.forward(plan.inverse(to_dev(cs, "c128")))
+    plan.sync_status()
+    back = back.cpu().numpy()
+    sel = two_l % 2 == 0
+    assert np.max(np.abs(back[sel] - cs[sel])) < 1e-12 * np.max(np.abs(cs))
+
+
+def test_determinism(su2):
+    N = 64
+    f = I.draw_grid_gaussian((N, N, N), np.random.default_rng(11))
+    plan = su2.Plan(N=N, batch=1, dtype="c64")
+    x = to_dev(f, "c64")
+    a = plan.forward(x).clone()
+    b = plan.forward(x).clone()
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+def test_rejects_bad_tensors(su2):
+    plan = su2.Plan(N=16, batch=1, dtype="c64")
+    with pytest.raises(ValueError):
+        plan.forward(torch.zeros(16 ** 3, dtype=torch.complex128, device="cuda"))
+    with pytest.raises(ValueError):
+        plan.forward(torch.zeros(17, dtype=torch.complex64, device="cuda"))
