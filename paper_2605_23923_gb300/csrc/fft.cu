@@ -166,6 +166,367 @@ fft_fwd_cluster(BandArgs a, const cplx<T>* __restrict__ grid, cplx<T>* __restric
 }
 
 // ---------------------------------------------------------------------------
+// Forward, persistent pipelined version (N = 64, 128, 256; complex64).
+// One cluster of C = N/32 CTAs walks over planes (function, beta node); CTA c
+// owns the 32 columns j2 in [32c, 32c+32).  The next plane's N x 32 column
+// slab is brought into a second shared buffer by 1-D bulk copies (TMA, one
+// 256-byte row each, completion on an mbarrier) while the current plane runs
+// both sectors through the four DFT passes, so loads overlap compute.
+// ---------------------------------------------------------------------------
+template <int N>
+struct PipeCfg {
+    static constexpr int C = N / 32;
+    static constexpr int W = 32;
+    static constexpr int R1 = Radix<N>::R1, R2 = Radix<N>::R2;
+    static constexpr int THREADS = (W * R1 > 512) ? 512 : W * R1;
+    static constexpr int LD1 = W + 1, LD2 = N + 1;
+    static constexpr int SLAB = N * W;
+    static constexpr int WBUF = (N * LD1 > W * LD2) ? N * LD1 : W * LD2;
+    static constexpr int F2S = 2 * SLAB + WBUF + N + 2 * N;       // float2 elements
+    static constexpr size_t smem_bytes() { return (size_t)F2S * sizeof(float2) + 2 * sizeof(uint64_t); }
+};
+
+template <int N>
+__global__ void __launch_bounds__(PipeCfg<N>::THREADS, 1)
+fft_fwd_pipe(BandArgs a, const float2* __restrict__ grid, float2* __restrict__ ws) {
+    using P = PipeCfg<N>;
+    constexpr int C = P::C, W = P::W, R1 = P::R1, R2 = P::R2, LD1 = P::LD1, LD2 = P::LD2;
+    constexpr int THREADS = P::THREADS, SLAB = P::SLAB;
+    static_assert(C >= 2, "cluster of at least two CTAs");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float2* S = reinterpret_cast<float2*>(smem_raw);       // [2][N][W] dense
+    float2* Wb = S + 2 * SLAB;                              // work buffer
+    float2* om = Wb + P::WBUF;                              // exp(+2 pi i t/N)
+    float2* tw2 = om + N;                                   // exp(i pi t/N), t < 2N
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(tw2 + 2 * N);
+
+    const int c = (int)cluster_ctarank();
+    const int q = blockIdx.x / C, nq = gridDim.x / C;
+    const int nplanes = a.nfunc * N;
+    const int tid = threadIdx.x, lane = tid & 31;
+
+    for (int t = tid; t < N; t += THREADS) om[t] = a.om32[t];
+    for (int t = tid; t < 2 * N; t += THREADS) {
+        const float2 z = a.twist32[t & (N - 1)];
+        tw2[t] = (t < N) ? z : make_float2(-z.x, -z.y);
+    }
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    auto issue = [&](int plane, int buf) {   // warp 0 only
+        const int f = a.fidx[plane / N], k = plane % N;
+        const float2* src = grid + a.grid_off[f] + (size_t)k * N + c * W;
+        float2* dst = S + buf * SLAB;
+        if (lane == 0) mbar_arrive_expect_tx(&mbar[buf], (uint32_t)(N * W * sizeof(float2)));
+        __syncwarp();
+        for (int j1 = lane; j1 < N; j1 += 32)
+            bulk_g2s(dst + j1 * W, src + (size_t)j1 * N * N, (uint32_t)(W * sizeof(float2)), &mbar[buf]);
+    };
+
+    if (q < nplanes && tid < 32) issue(q, 0);
+    int it = 0;
+    for (int plane = q; plane < nplanes; plane += nq, ++it) {
+        const int buf = it & 1;
+        const int next = plane + nq;
+        if (next < nplanes && tid < 32) {
+            fence_proxy_async_smem();
+            issue(next, buf ^ 1);
+        }
+        const int f = a.fidx[plane / N], k = plane % N;
+        mbar_wait_bounded(&mbar[buf], (uint32_t)((it >> 1) & 1), a.err);
+        const float2* Sb = S + buf * SLAB;
+        float2* out_plane = ws + a.ws_off[f] + (size_t)k * 2 * N * N;
+        const float scale = a.w32[k] / (2.f * (float)N * (float)N);
+
+        for (int s = 0; s < 2; ++s) {
+            // Pass 1A: column DFT over j1, stride-R1 part (sector 1 pre-twisted).
+#pragma unroll
+            for (int task = tid; task < W * R1; task += THREADS) {
+                const int jc = task % W, ia = task / W;
+                const int j2 = c * W + jc;
+                float2 v[R2];
+#pragma unroll
+                for (int b = 0; b < R2; ++b) v[b] = Sb[(ia + R1 * b) * W + jc];
+                if (s) {
+#pragma unroll
+                    for (int b = 0; b < R2; ++b) v[b] = cmul(v[b], tw2[ia + R1 * b + j2]);
+                }
+                dft_reg<R2, 1, float>(v);
+#pragma unroll
+                for (int qb = 0; qb < R2; ++qb)
+                    Wb[(ia + R1 * qb) * LD1 + jc] = (qb == 0) ? v[0] : cmul(v[qb], om[ia * qb]);
+            }
+            __syncthreads();
+            // Pass 1B: contiguous R1-point DFTs; bin p = qb + R2*qa in row qa + R1*qb.
+#pragma unroll
+            for (int task = tid; task < W * R2; task += THREADS) {
+                const int jc = task % W, qb = task / W;
+                float2 v[R1];
+#pragma unroll
+                for (int ia = 0; ia < R1; ++ia) v[ia] = Wb[(ia + R1 * qb) * LD1 + jc];
+                dft_reg<R1, 1, float>(v);
+#pragma unroll
+                for (int qa = 0; qa < R1; ++qa) Wb[(qa + R1 * qb) * LD1 + jc] = v[qa];
+            }
+            cluster_arrive_release();
+            cluster_wait_acquire();
+            // Pass 2A: gather the owned rows p from every CTA of the cluster.
+            constexpr int NT2 = (W * R1 + THREADS - 1) / THREADS;
+            float2 hold[NT2][R2];
+#pragma unroll
+            for (int i2 = 0; i2 < NT2; ++i2) {
+                const int task = tid + i2 * THREADS;
+                if (task < W * R1) {
+                    const int pl = task % W, ia = task / W;
+                    const int p = c * W + pl;
+                    const int rowp = p / R2 + R1 * (p % R2);
+                    float2 v[R2];
+#pragma unroll
+                    for (int b = 0; b < R2; ++b) {
+                        const int j2 = ia + R1 * b;
+                        v[b] = ld_dsmem(map_shared(&Wb[rowp * LD1 + (j2 % W)], (unsigned)(j2 / W)), float2());
+                    }
+                    dft_reg<R2, 1, float>(v);
+#pragma unroll
+                    for (int qb = 0; qb < R2; ++qb) hold[i2][qb] = (qb == 0) ? v[0] : cmul(v[qb], om[ia * qb]);
+                }
+            }
+            cluster_arrive_release();
+            cluster_wait_acquire();
+#pragma unroll
+            for (int i2 = 0; i2 < NT2; ++i2) {
+                const int task = tid + i2 * THREADS;
+                if (task < W * R1) {
+                    const int pl = task % W, ia = task / W;
+#pragma unroll
+                    for (int qb = 0; qb < R2; ++qb) Wb[pl * LD2 + ia + R1 * qb] = hold[i2][qb];
+                }
+            }
+            __syncthreads();
+            // Pass 2B: R1-point DFTs, scale, sign and store (n fastest).
+            float2* out = out_plane + (size_t)s * N * N;
+#pragma unroll
+            for (int task = tid; task < W * R2; task += THREADS) {
+                const int pl = task % W, qb = task / W;
+                const int p = c * W + pl;
+                float2 v[R1];
+#pragma unroll
+                for (int ia = 0; ia < R1; ++ia) v[ia] = Wb[pl * LD2 + ia + R1 * qb];
+                dft_reg<R1, 1, float>(v);
+                const int ni = (p + N / 2) & (N - 1);
+                // parity of mi = (qb + R2*qa + N/2) mod N equals the parity of qb
+                float sc = ((ni + qb) & 1) ? -scale : scale;
+                if (s) sc = -sc;
+                const bool zero_col = (s == 0 && ni == 0);
+#pragma unroll
+                for (int qa = 0; qa < R1; ++qa) {
+                    const int qq = qb + R2 * qa;
+                    const int mi = (qq + N / 2) & (N - 1);
+                    float2 val = make_float2(v[qa].x * sc, v[qa].y * sc);
+                    if (zero_col || (s == 0 && mi == 0)) val = make_float2(0.f, 0.f);
+                    out[(size_t)mi * N + ni] = val;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Forward, persistent version with a bulk-copy exchange (N = 64, 128, 256;
+// complex64).  Work items are (function, beta node, sector); one cluster of
+// C = N/16 CTAs takes items q, q + nq, ...  CTA c holds the 16 columns
+// j2 in [16c, 16c+16) of the item's N x N plane:
+//   S[2]  column slabs, filled by 1-D bulk copies (TMA) one item ahead;
+//   1A/1B column DFTs over j1 in place in S;
+//   push  every row p of the result goes, as one 128-byte bulk copy between
+//         shared memories, to the CTA owning p (c' = p/16), completion counted
+//         on that CTA's mbarrier;
+//   R     the received 16 rows (all N columns); 2A/2B row DFTs over j2, the
+//         2A result written back with an XOR swizzle so that 2B reads one
+//         column across 16 rows without bank conflicts; 2B stores F2 rows.
+// One cluster barrier per item, split: arrive after 2B (my R is free and I
+// have received the item, so every sender's slab is free), wait after the
+// next item's column passes (before pushing into other CTAs' R and before
+// refilling the slab the previous push read).
+// ---------------------------------------------------------------------------
+template <int N>
+struct XCfg {
+    static constexpr int W = 16;
+    static constexpr int C = N / W;
+    static constexpr int R1 = Radix<N>::R1, R2 = Radix<N>::R2;
+    static constexpr int THREADS = 256;
+    static constexpr int SLAB = N * W;                      // float2 per slab
+    static constexpr int F2S = 2 * SLAB + W * N + N + 2 * N;
+    static constexpr size_t smem_bytes() { return (size_t)F2S * sizeof(float2) + 3 * sizeof(uint64_t); }
+};
+
+template <int N>
+__global__ void __launch_bounds__(256, 2)
+fft_fwd_xchg(BandArgs a, const float2* __restrict__ grid, float2* __restrict__ ws) {
+    using P = XCfg<N>;
+    constexpr int C = P::C, W = P::W, R1 = P::R1, R2 = P::R2, THREADS = P::THREADS, SLAB = P::SLAB;
+    static_assert(C >= 2 && C <= 16, "cluster size");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float2* S = reinterpret_cast<float2*>(smem_raw);       // [2][N][W]
+    float2* R = S + 2 * SLAB;                               // [W][N] (swizzled after 2A)
+    float2* om = R + W * N;                                 // exp(+2 pi i t/N)
+    float2* tw2 = om + N;                                   // exp(i pi t/N), t < 2N
+    uint64_t* mbS = reinterpret_cast<uint64_t*>(tw2 + 2 * N);   // [2]
+    uint64_t* mbR = mbS + 2;
+
+    const int c = (int)cluster_ctarank();
+    const int q = blockIdx.x / C, nq = gridDim.x / C;
+    const int nitems = a.nfunc * N * 2;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    for (int t = tid; t < N; t += THREADS) om[t] = a.om32[t];
+    for (int t = tid; t < 2 * N; t += THREADS) {
+        const float2 z = a.twist32[t & (N - 1)];
+        tw2[t] = (t < N) ? z : make_float2(-z.x, -z.y);
+    }
+    if (tid == 0) {
+        mbar_init(&mbS[0], 1);
+        mbar_init(&mbS[1], 1);
+        mbar_init(mbR, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    // every CTA's barriers are initialised before any remote copy can target them
+    cluster_arrive_release();
+    cluster_wait_acquire();
+
+    auto load_slab = [&](int item, int buf) {      // warp 0
+        const int plane = item >> 1;
+        const int f = a.fidx[plane / N], k = plane % N;
+        const float2* src = grid + a.grid_off[f] + (size_t)k * N + c * W;
+        float2* dst = S + buf * SLAB;
+        if (lane == 0) mbar_arrive_expect_tx(&mbS[buf], (uint32_t)(SLAB * sizeof(float2)));
+        __syncwarp();
+        for (int j1 = lane; j1 < N; j1 += 32)
+            bulk_g2s(dst + j1 * W, src + (size_t)j1 * N * N, (uint32_t)(W * sizeof(float2)), &mbS[buf]);
+    };
+
+    if (q < nitems && warp == 0) load_slab(q, 0);
+    int it = 0;
+    for (int item = q; item < nitems; item += nq, ++it) {
+        const int buf = it & 1;
+        const int s = item & 1, plane = item >> 1;
+        const int f = a.fidx[plane / N], k = plane % N;
+        float2* Sb = S + buf * SLAB;
+        mbar_wait_bounded(&mbS[buf], (uint32_t)((it >> 1) & 1), a.err);
+
+        // Pass 1A: column DFT over j1, stride-R1 part, in place (sector 1 pre-twisted).
+#pragma unroll
+        for (int task = tid; task < W * R1; task += THREADS) {
+            const int jc = task % W, ia = task / W;
+            const int j2 = c * W + jc;
+            float2 v[R2];
+#pragma unroll
+            for (int b = 0; b < R2; ++b) v[b] = Sb[(ia + R1 * b) * W + jc];
+            if (s) {
+#pragma unroll
+                for (int b = 0; b < R2; ++b) v[b] = cmul(v[b], tw2[ia + R1 * b + j2]);
+            }
+            dft_reg<R2, 1, float>(v);
+#pragma unroll
+            for (int qb = 0; qb < R2; ++qb)
+                Sb[(ia + R1 * qb) * W + jc] = (qb == 0) ? v[0] : cmul(v[qb], om[ia * qb]);
+        }
+        __syncthreads();
+        // Pass 1B: R1-point DFTs in place; bin p = qb + R2*qa sits in row qa + R1*qb.
+#pragma unroll
+        for (int task = tid; task < W * R2; task += THREADS) {
+            const int jc = task % W, qb = task / W;
+            float2 v[R1];
+#pragma unroll
+            for (int ia = 0; ia < R1; ++ia) v[ia] = Sb[(ia + R1 * qb) * W + jc];
+            dft_reg<R1, 1, float>(v);
+#pragma unroll
+            for (int qa = 0; qa < R1; ++qa) Sb[(qa + R1 * qb) * W + jc] = v[qa];
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (it > 0) cluster_wait_acquire();
+        if (warp == 0) {
+            const int next = item + nq;
+            if (next < nitems) {
+                fence_proxy_async_smem();
+                load_slab(next, buf ^ 1);
+            }
+        } else if (warp == 1) {
+            // push row p (storage row p/R2 + R1*(p%R2)) to CTA p/W, row p%W, columns [cW, cW+W)
+            if (lane == 0) mbar_arrive_expect_tx(mbR, (uint32_t)(W * N * sizeof(float2)));
+            for (int p = lane; p < N; p += 32) {
+                const int row = p / R2 + R1 * (p % R2);
+                bulk_s2s_remote(R + (p % W) * N + c * W, Sb + row * W, (uint32_t)(W * sizeof(float2)), mbR,
+                                (unsigned)(p / W));
+            }
+        }
+        mbar_wait_bounded(mbR, (uint32_t)(it & 1), a.err);
+
+        // Pass 2A: row DFT over j2, stride-R1 part; lanes run along the row.
+        constexpr int NT2 = (W * R1 + THREADS - 1) / THREADS;
+        float2 hold[NT2][R2];
+#pragma unroll
+        for (int i2 = 0; i2 < NT2; ++i2) {
+            const int task = tid + i2 * THREADS;
+            if (task < W * R1) {
+                const int ia = task % R1, pl = task / R1;
+                float2 v[R2];
+#pragma unroll
+                for (int b = 0; b < R2; ++b) v[b] = R[pl * N + ia + R1 * b];
+                dft_reg<R2, 1, float>(v);
+#pragma unroll
+                for (int qb = 0; qb < R2; ++qb) hold[i2][qb] = (qb == 0) ? v[0] : cmul(v[qb], om[ia * qb]);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i2 = 0; i2 < NT2; ++i2) {
+            const int task = tid + i2 * THREADS;
+            if (task < W * R1) {
+                const int ia = task % R1, pl = task / R1;
+#pragma unroll
+                for (int qb = 0; qb < R2; ++qb) R[pl * N + ((ia + R1 * qb) ^ (pl & 15))] = hold[i2][qb];
+            }
+        }
+        __syncthreads();
+        // Pass 2B: R1-point DFTs, scale, sign, store F2 (16 consecutive n per half-warp).
+        const float scale = a.w32[k] / (2.f * (float)N * (float)N);
+        float2* out = ws + a.ws_off[f] + ((size_t)k * 2 + s) * N * N;
+#pragma unroll
+        for (int task = tid; task < W * R2; task += THREADS) {
+            const int pl = task % W, qb = task / W;
+            const int p = c * W + pl;
+            float2 v[R1];
+#pragma unroll
+            for (int ia = 0; ia < R1; ++ia) v[ia] = R[pl * N + ((ia + R1 * qb) ^ (pl & 15))];
+            dft_reg<R1, 1, float>(v);
+            const int ni = (p + N / 2) & (N - 1);
+            float sc = ((ni + qb) & 1) ? -scale : scale;     // parity of mi = parity of qb
+            if (s) sc = -sc;
+            const bool zero_col = (s == 0 && ni == 0);
+#pragma unroll
+            for (int qa = 0; qa < R1; ++qa) {
+                const int qq = qb + R2 * qa;
+                const int mi = (qq + N / 2) & (N - 1);
+                float2 val = make_float2(v[qa].x * sc, v[qa].y * sc);
+                if (zero_col || (s == 0 && mi == 0)) val = make_float2(0.f, 0.f);
+                out[(size_t)mi * N + ni] = val;
+            }
+        }
+        fence_proxy_async_smem();
+        cluster_arrive_release();
+    }
+    if (it > 0) cluster_wait_acquire();
+}
+
+// ---------------------------------------------------------------------------
 // Inverse, cluster version.  CTA c owns the n-bins p in [32c, 32c+32) for pass 1
 // and the output columns j2 in [32c, 32c+32) for pass 2; both sectors are
 // accumulated in registers before the single store.
@@ -416,6 +777,74 @@ static cudaError_t launch_cluster(const BandArgs& a, const void* in, void* out, 
     return cudaLaunchKernelEx(&cfg, kern, a, (const cplx<T>*)in, (cplx<T>*)out);
 }
 
+template <int N>
+static cudaError_t launch_pipe(const BandArgs& a, const void* in, void* out, cudaStream_t st) {
+    using P = PipeCfg<N>;
+    auto kern = fft_fwd_pipe<N>;
+    const size_t smem = P::smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    static int max_clusters = 0;      // per N, per process (the device's cluster capacity)
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = P::C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(P::THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (max_clusters == 0) {
+        cfg.gridDim = dim3(P::C * 1024, 1, 1);
+        int n = 0;
+        e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg);
+        if (e != cudaSuccess) return e;
+        max_clusters = n > 0 ? n : 1;
+    }
+    const int nplanes = a.nfunc * N;
+    const int ncl = nplanes < max_clusters ? nplanes : max_clusters;
+    cfg.gridDim = dim3(P::C * ncl, 1, 1);
+    return cudaLaunchKernelEx(&cfg, kern, a, (const float2*)in, (float2*)out);
+}
+
+template <int N>
+static cudaError_t launch_xchg(const BandArgs& a, const void* in, void* out, cudaStream_t st) {
+    using P = XCfg<N>;
+    auto kern = fft_fwd_xchg<N>;
+    const size_t smem = P::smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (P::C > 8) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    static int max_clusters = 0;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = P::C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(P::THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (max_clusters == 0) {
+        cfg.gridDim = dim3(P::C * 512, 1, 1);
+        int n = 0;
+        e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg);
+        if (e != cudaSuccess) return e;
+        max_clusters = n > 0 ? n : 1;
+    }
+    const int nitems = a.nfunc * N * 2;
+    const int ncl = nitems < max_clusters ? nitems : max_clusters;
+    cfg.gridDim = dim3(P::C * ncl, 1, 1);
+    return cudaLaunchKernelEx(&cfg, kern, a, (const float2*)in, (float2*)out);
+}
+
 template <typename T, bool FWD>
 static cudaError_t launch_any(const BandArgs& a, const void* in, void* out, cudaStream_t st) {
     if (a.nfunc <= 0) return cudaSuccess;
@@ -427,9 +856,15 @@ static cudaError_t launch_any(const BandArgs& a, const void* in, void* out, cuda
             return cudaGetLastError();
         }
         case 32: return launch_cluster<T, 32, 1, 128, FWD>(a, in, out, st);
-        case 64: return launch_cluster<T, 64, 2, 256, FWD>(a, in, out, st);
-        case 128: return launch_cluster<T, 128, 4, 256, FWD>(a, in, out, st);
-        case 256: return launch_cluster<T, 256, 8, 256, FWD>(a, in, out, st);
+        case 64:
+            if constexpr (FWD && sizeof(T) == 4) return launch_xchg<64>(a, in, out, st);
+            else return launch_cluster<T, 64, 2, 256, FWD>(a, in, out, st);
+        case 128:
+            if constexpr (FWD && sizeof(T) == 4) return launch_xchg<128>(a, in, out, st);
+            else return launch_cluster<T, 128, 4, 256, FWD>(a, in, out, st);
+        case 256:
+            if constexpr (FWD && sizeof(T) == 4) return launch_xchg<256>(a, in, out, st);
+            else return launch_cluster<T, 256, 8, 256, FWD>(a, in, out, st);
         case 512:
             if constexpr (sizeof(T) == 4) return launch_cluster<T, 512, 16, 512, FWD>(a, in, out, st);
             else return cudaErrorInvalidValue;
