@@ -211,15 +211,19 @@ def main():
         build.build()
 
     N, B = args.N, args.batch
-    algo = args.algo
-    if algo == "auto":
-        algo = "fp32"
+    algos = []
+    if args.algo in ("auto", "tc_bf16x3"):
         try:
             su2.Plan(N=N, batch=1, dtype="c64", algo="tc_bf16x3").close()
-            algo = "tc_bf16x3"
+            algos.append("tc_bf16x3")
         except su2.SU2Error:
-            pass
-    plan = su2.Plan(N=N, batch=B, dtype="c64", algo=algo)
+            if args.algo == "tc_bf16x3":
+                raise
+    if args.algo in ("auto", "fp32") or not algos:
+        algos.append("fp32")
+    algo = algos[0]                      # headline path
+    plans = {al: su2.Plan(N=N, batch=B, dtype="c64", algo=al) for al in algos}
+    plan = plans[algo]
     stream = torch.cuda.current_stream()
 
     # ---- inputs: seeded coefficients -> grids by the library's synthesis
@@ -230,56 +234,68 @@ def main():
         c = I.draw_coeffs(N, rng, "inv1").astype(np.complex64)
         coeffs[b * C:(b + 1) * C].copy_(torch.from_numpy(c))
     grid = torch.empty(B * N ** 3, dtype=torch.complex64, device=dev)
+    ws = plan.workspace()
+    for al in algos:
+        plans[al]._ws = ws               # one shared workspace
     syn = su2.Plan(N=N, batch=B, dtype="c64", algo="fp32")
-    syn.inverse(coeffs, out=grid, ws=plan.workspace())
+    syn.inverse(coeffs, out=grid, ws=ws)
     syn.sync_status()
     syn.close()
     del coeffs
-    out = torch.empty(B * C, dtype=torch.complex64, device=dev)
-    ws = plan.workspace()
+    outs = {al: torch.empty(B * C, dtype=torch.complex64, device=dev) for al in algos}
 
-    def step(ev=None):
-        if ev is None:
-            plan.forward_stage1(grid, ws=ws, stream=stream)
-            plan.forward_stage2(out=out, ws=ws, stream=stream)
-        else:
-            ev[0].record(stream)
-            plan.forward_stage1(grid, ws=ws, stream=stream)
-            ev[1].record(stream)
-            plan.forward_stage2(out=out, ws=ws, stream=stream)
-            ev[2].record(stream)
+    def time_path(al, with_clocks):
+        pl, out = plans[al], outs[al]
 
-    for _ in range(args.warmup):
-        step()
-    plan.sync_status()
+        def step(ev=None):
+            if ev is not None:
+                ev[0].record(stream)
+            pl.forward_stage1(grid, ws=ws, stream=stream)
+            if ev is not None:
+                ev[1].record(stream)
+            pl.forward_stage2(out=out, ws=ws, stream=stream)
+            if ev is not None:
+                ev[2].record(stream)
 
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
-    clocks = ClockSampler(local)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    time.sleep(0.3)
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    t_start.record(stream)
-    for i in range(args.steps):
-        step(evs[i])
-    t_end.record(stream)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    if world > 1:
-        dist.barrier()
-    plan.sync_status()
-    elapsed_ms = t_start.elapsed_time(t_end)
-    st1 = [e[0].elapsed_time(e[1]) for e in evs]
-    st2 = [e[1].elapsed_time(e[2]) for e in evs]
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+        for _ in range(args.warmup):
+            step()
+        pl.sync_status()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+        clocks = ClockSampler(local) if with_clocks else None
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for i in range(args.steps):
+            step(evs[i])
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop() if clocks else None
+        if world > 1:
+            dist.barrier()
+        pl.sync_status()
+        el = t_start.elapsed_time(t_end)
+        if world > 1:
+            t = torch.tensor([el], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        return {"elapsed_ms": el, "st1": [e[0].elapsed_time(e[1]) for e in evs],
+                "st2": [e[1].elapsed_time(e[2]) for e in evs], "clocks": clk}
+
+    res = {al: time_path(al, al == algo) for al in algos}
+    elapsed_ms = res[algo]["elapsed_ms"]
+    st1, st2, clk = res[algo]["st1"], res[algo]["st2"], res[algo]["clocks"]
     ms_per_step = elapsed_ms / args.steps
     value = world * B * args.steps / (elapsed_ms / 1e3)
+    path_diff = None
+    if len(algos) > 1:
+        a0, a1 = outs[algos[0]], outs[algos[1]]
+        path_diff = float(((a0 - a1).abs().max() / a1.abs().max()).item())
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -288,6 +304,7 @@ def main():
         host_grid.copy_(grid)
         host_out = torch.empty(B * C, dtype=torch.complex64, pin_memory=True)
         dgrid = torch.empty_like(grid)
+        out = outs[algo]
 
         def e2e_step():
             dgrid.copy_(host_grid, non_blocking=True)
@@ -322,30 +339,40 @@ def main():
 
     # ---- roofline of the dominant kernel
     peaks, peak_src = measured_peaks()
-    s1 = statistics.mean(st1) / 1e3
-    s2 = statistics.mean(st2) / 1e3
     fft_bytes = B * (8 * N ** 3 + 8 * (2 * N * N - 2 * N + 1) * N)
-    fft_gbs = fft_bytes / s1 / 1e9
     contr_flops = B * 4 * N * C
     contr_bytes = B * (8 * (2 * N * N - 2 * N + 1) * N + 8 * C)
-    sm_mhz = clk["sm_mhz"] if clk else peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = SMS * FP32_LANES * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    stages = {
-        "stage1_fft": {"ms": s1 * 1e3, "GB/s": fft_gbs, "bound": "hbm",
-                       "frac": fft_gbs / peaks["hbm_gbs"], "alg_bytes": fft_bytes},
-        "stage2_contraction": {"ms": s2 * 1e3, "algo": algo, "alg_flops": contr_flops,
-                               "TFLOP/s": contr_flops / s2 / 1e12, "GB/s": contr_bytes / s2 / 1e9,
-                               "alg_bytes": contr_bytes},
-    }
-    if algo == "fp32":
-        stages["stage2_contraction"].update(bound="alu", peak_tflops=fp32_peak,
-                                            frac=contr_flops / s2 / 1e12 / fp32_peak)
-    else:
-        stages["stage2_contraction"].update(bound="hbm", frac=contr_bytes / s2 / 1e9 / peaks["hbm_gbs"])
+
+    def stage_report(al):
+        r = res[al]
+        s1 = statistics.mean(r["st1"]) / 1e3
+        s2 = statistics.mean(r["st2"]) / 1e3
+        fft_gbs = fft_bytes / s1 / 1e9
+        out = {
+            "ms_per_step": r["elapsed_ms"] / args.steps,
+            "value": world * B * args.steps / (r["elapsed_ms"] / 1e3),
+            "stage1_fft": {"ms": s1 * 1e3, "GB/s": fft_gbs, "bound": "hbm", "frac": fft_gbs / peaks["hbm_gbs"],
+                           "alg_bytes": fft_bytes},
+            "stage2_contraction": {"ms": s2 * 1e3, "algo": al, "alg_flops": contr_flops,
+                                   "TFLOP/s": contr_flops / s2 / 1e12, "GB/s": contr_bytes / s2 / 1e9,
+                                   "alg_bytes": contr_bytes},
+        }
+        if al == "fp32":
+            out["stage2_contraction"].update(bound="alu", peak_tflops=fp32_peak,
+                                             frac=contr_flops / s2 / 1e12 / fp32_peak)
+        else:
+            out["stage2_contraction"].update(bound="hbm",
+                                             frac=contr_bytes / s2 / 1e9 / peaks["hbm_gbs"],
+                                             tensor_tflops_bf16x3=3 * contr_flops / s2 / 1e12)
+        return out, s1, s2, fft_gbs
+
+    stages, s1, s2, fft_gbs = stage_report(algo)
+    others = {al: stage_report(al)[0] for al in algos if al != algo}
     if s1 >= s2:
         roof = {"bound": "hbm", "achieved": fft_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": fft_gbs / peaks["hbm_gbs"], "traffic": None, "kernel": "stage-1 2-D DFT (fft_fwd_cluster)",
-                "peak_source": peak_src}
+                "frac": fft_gbs / peaks["hbm_gbs"], "traffic": None,
+                "kernel": "stage-1 2-D DFT (fft_fwd_xchg)", "peak_source": peak_src}
     elif algo == "fp32":
         ach = contr_flops / s2 / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
@@ -354,8 +381,8 @@ def main():
     else:
         ach = contr_bytes / s2 / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": "stage-2 TC contraction",
-                "peak_source": peak_src}
+                "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                "kernel": "stage-2 tensor-core contraction (contract_tc_kernel)", "peak_source": peak_src}
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -372,9 +399,11 @@ def main():
                    "parallelism": f"replicas x{world} (no collective)"},
         "roofline": roof,
         "stages": stages,
+        "other_paths": others,
+        "tc_vs_fp32_max_rel_diff": path_diff,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": 2 * args.steps,  # stage-1 + stage-2 launch per step (headline path)
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)

@@ -181,6 +181,7 @@ su2::BandArgs band_args(const su2_plan_s* P, const Band& b) {
     a.twist32 = b.d_twist32;
     a.twist64 = b.d_twist64;
     a.err = P->d_err;
+    a.ws_group_off = b.fids.empty() ? 0 : P->ws_off[b.fids[0]];
     return a;
 }
 
@@ -252,12 +253,19 @@ su2_status su2_plan(su2_plan_t* out, const su2_plan_desc* desc) {
         const size_t N = (size_t)Ns[f];
         P->grid_off[f] = P->grid_total;
         P->coeff_off[f] = P->coeff_total;
-        P->ws_off[f] = P->ws_total;
         P->grid_total += N * N * N;
         P->coeff_total += ncoef((int)N);
-        P->ws_total += 2 * N * N * N;
         P->bands[(int)N].fids.push_back(f);
         Nmax = std::max(Nmax, (int)N);
+    }
+    // stage-1 planes: contiguous per bandwidth group, functions in batch order,
+    // so that a group's planes form one regularly strided array
+    for (auto& kv : P->bands) {
+        const size_t N = (size_t)kv.first;
+        for (int f : kv.second.fids) {
+            P->ws_off[f] = P->ws_total;
+            P->ws_total += 2 * N * N * N;
+        }
     }
     std::vector<double> lf2(2 * Nmax + 2);
     for (size_t k = 0; k < lf2.size(); ++k) lf2[k] = lgamma((double)k + 1.0) / log(2.0);

@@ -299,6 +299,7 @@ struct BandArgs {
     const float2* twist32;        // exp(+i pi t/N), t = 0..N-1
     const double2* twist64;
     int* err;                     // device error word
+    size_t ws_group_off;          // stage-1 plane offset of the group's first function
 };
 
 }  // namespace su2

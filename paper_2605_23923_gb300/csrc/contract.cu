@@ -27,141 +27,10 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "recurrence.cuh"
 #include "su2_internal.h"
 
 namespace su2 {
-
-template <typename T> struct StepCoef { T A, C, bh, bl; };
-
-__device__ __forceinline__ size_t block_offset(int J) {
-    const size_t j = (size_t)J;
-    return j * (j + 1) * (2 * j + 1) / 6;
-}
-
-// Step coefficients for advancing from 2l = J to J + 2 for the pair (n2, m2).
-template <typename T>
-__device__ __forceinline__ StepCoef<T> step_coef(int J, int n2, int m2) {
-    StepCoef<T> c;
-    const T p1 = T((J + 2) * (J + 2) - n2 * n2), q1 = T((J + 2) * (J + 2) - m2 * m2);
-    const T rs = sqrt(p1) * sqrt(q1);
-    c.A = T(2 * (J + 2) * (J + 1)) / rs;
-    if (J == 0) {
-        c.C = T(0); c.bh = T(0); c.bl = T(0);
-    } else {
-        const int ip0 = J * J - n2 * n2, iq0 = J * J - m2 * m2;
-        const T p0 = T(ip0 > 0 ? ip0 : 0), q0 = T(iq0 > 0 ? iq0 : 0);
-        c.C = (T(J + 2) / T(J)) * (sqrt(p0) * sqrt(q0)) / rs;
-        const T num = T(n2 * m2), den = T(J * (J + 2));
-        c.bh = num / den;
-        c.bl = fma(-c.bh, den, num) / den;       // exact remainder of the division
-    }
-    return c;
-}
-
-// log2 |d^mu_{nm}(beta_k)| and its sign (Rodrigues-type formula at l = mu).
-__device__ __forceinline__ double seed_log2(const BandArgs& a, int n2, int m2, int k, double* sgn) {
-    const int mu2 = max(abs(n2), abs(m2));
-    int other, pc, ps;
-    double sg = 1.0;
-    if (abs(n2) == mu2 && (n2 > 0 || mu2 == 0)) {
-        other = m2; pc = (mu2 + m2) / 2; ps = (mu2 - m2) / 2;
-        if (((mu2 - m2) / 2) & 1) sg = -1.0;
-    } else if (n2 == -mu2) {
-        other = m2; pc = (mu2 - m2) / 2; ps = (mu2 + m2) / 2;
-    } else if (m2 == mu2) {
-        other = n2; pc = (mu2 + n2) / 2; ps = (mu2 - n2) / 2;
-    } else {
-        other = n2; pc = (mu2 - n2) / 2; ps = (mu2 + n2) / 2;
-        if (((mu2 + n2) / 2) & 1) sg = -1.0;
-    }
-    double L = 0.5 * (a.lf2[mu2] - a.lf2[(mu2 + other) / 2] - a.lf2[(mu2 - other) / 2]);
-    if (pc) L += (double)pc * a.log2c[k];
-    if (ps) L += (double)ps * a.log2s[k];
-    *sgn = sg;
-    return L;
-}
-
-// Recurrence state for one (pair, node).
-template <typename T> struct Rec;
-
-template <> struct Rec<float> {
-    float cur, prev, xh, xl;
-    int E;
-    __device__ __forceinline__ void seed(const BandArgs& a, int n2, int m2, int k) {
-        double sg;
-        const double L = seed_log2(a, n2, m2, k, &sg);
-        prev = 0.f;
-        const float2 xs = a.xsplit[k];
-        xh = xs.x; xl = xs.y;
-        if (!(L > -1e300)) { cur = 0.f; E = 0; return; }      // a zero power of a zero base
-        int e = 0;
-        if (L < -60.0) e = (int)ceil((-L - 60.0) / 120.0);
-        const double t = L + 120.0 * e;                        // in [-60, 60)
-        const double ti = floor(t);
-        const float mant = exp2f((float)(t - ti));
-        cur = (float)sg * ldexpf(mant, (int)ti);
-        E = e;
-    }
-    __device__ __forceinline__ float value() const { return E == 0 ? cur : 0.f; }
-    __device__ __forceinline__ void step(const StepCoef<float>& c) {
-        const float xb = (xh - c.bh) + (xl - c.bl);
-        float nxt = fmaf(c.A * xb, cur, -c.C * prev);
-        if (E > 0 && fabsf(nxt) >= 1.152921504606847e18f) {   // 2^60
-            nxt *= 7.52316384526264e-37f;                        // 2^-120
-            cur *= 7.52316384526264e-37f;
-            --E;
-        }
-        prev = cur;
-        cur = nxt;
-    }
-};
-
-template <> struct Rec<double> {
-    double cur, prev, x;
-    __device__ __forceinline__ void seed(const BandArgs& a, int n2, int m2, int k) {
-        double sg;
-        const double L = seed_log2(a, n2, m2, k, &sg);
-        prev = 0.0;
-        x = a.cosb[k];
-        cur = (L > -1e300) ? sg * exp2(L) : 0.0;
-    }
-    __device__ __forceinline__ double value() const { return cur; }
-    __device__ __forceinline__ void step(const StepCoef<double>& c) {
-        const double nxt = c.A * (x - c.bh) * cur - c.C * prev;
-        prev = cur;
-        cur = nxt;
-    }
-};
-
-// Decoded tile: sector s, fixed m, NB consecutive n.
-template <int NB>
-struct Tile {
-    int s, mi, nb, m2, jtop, j0, L;
-    int n2[NB], mu2[NB];
-    bool valid[NB];
-    bool any;
-    __device__ __forceinline__ void decode(int N, int t) {
-        const int nbk = N / NB;
-        nb = t % nbk; t /= nbk;
-        mi = t % N; t /= N;
-        s = t;
-        m2 = 2 * (mi - N / 2) + s;
-        jtop = N - 2 + s;
-        j0 = 1 << 30;
-        any = !(s == 0 && mi == 0);
-        bool some = false;
-#pragma unroll
-        for (int p = 0; p < NB; ++p) {
-            const int ni = nb * NB + p;
-            n2[p] = 2 * (ni - N / 2) + s;
-            valid[p] = any && !(s == 0 && ni == 0);
-            mu2[p] = max(abs(n2[p]), abs(m2));
-            if (valid[p]) { j0 = min(j0, mu2[p]); some = true; }
-        }
-        any = some;
-        L = any ? (jtop - j0) / 2 + 1 : 0;
-    }
-};
 
 template <typename T> __device__ __forceinline__ void store4(T* dst, const T (&v)[4]);
 template <> __device__ __forceinline__ void store4<float>(float* dst, const float (&v)[4]) {

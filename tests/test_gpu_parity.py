@@ -218,3 +218,76 @@ def test_rejects_bad_tensors(su2):
         plan.forward(torch.zeros(16 ** 3, dtype=torch.complex128, device="cuda"))
     with pytest.raises(ValueError):
         plan.forward(torch.zeros(17, dtype=torch.complex64, device="cuda"))
+
+
+# ---------------------------------------------------------------------------
+# Tensor-core (split-BF16) contraction
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("B", [1, 3])
+def test_forward_tc_n64(su2, B):
+    N = 64
+    rng = np.random.default_rng(400 + B)
+    grids = [cast(I.draw_grid_gaussian((N, N, N), rng), "c64") for _ in range(B)]
+    _, outs = run_forward(su2, grids, "c64", algo="tc_bf16x3")
+    for g, o in zip(grids, outs):
+        assert rel(o, T.forward_separable(g)) < TOL32, rel(o, T.forward_separable(g))
+
+
+def test_forward_tc_bandlimited_n64(su2):
+    N = 64
+    rng = np.random.default_rng(1)
+    c = I.draw_coeffs(N, rng, "inv2")
+    f = cast(T.inverse_separable(c, N) + I.draw_grid_noise((N, N, N), 0.01, rng), "c64")
+    _, (got,) = run_forward(su2, [f], "c64", algo="tc_bf16x3")
+    assert rel(got, T.forward_separable(f)) < TOL32
+
+
+def test_forward_tc_ragged(su2):
+    Ns = [64, 128, 64]
+    rng = np.random.default_rng(12)
+    grids = [cast(I.draw_grid_gaussian((n, n, n), rng), "c64") for n in Ns]
+    _, outs = run_forward(su2, grids, "c64", Ns=Ns, algo="tc_bf16x3")
+    from oracle import grid as G
+    for n, g, o in zip(Ns, grids, outs):
+        if n == 64:
+            assert rel(o, T.forward_separable(g)) < TOL32
+        else:
+            worst = scale = 0.0
+            for n2, m2 in [(0, 0), (126, -126), (127, 127), (-5, 3), (44, 44), (-1, -127)]:
+                j0, vals = T.forward_pair(g, n2, m2)
+                for i, v in enumerate(vals):
+                    worst = max(worst, abs(o[G.coeff_index(j0 + 2 * i, m2, n2)] - v))
+                    scale = max(scale, abs(v))
+            assert worst / scale < TOL32
+
+
+@pytest.mark.parametrize("algo", ["fp32", "tc_bf16x3"])
+def test_full_size_n256_b64_sampled(su2, algo):
+    """The benchmark's launch configuration (N = 256, 64 functions, complex64):
+    4 seeded grids tiled over the 64 batch slots; sampled (m, n) pairs of every
+    slot against the oracle's per-pair transform."""
+    N, B = 256, 64
+    rng = np.random.default_rng(2)
+    base = [I.draw_grid_gaussian((N, N, N), rng).astype(np.complex64) for _ in range(4)]
+    plan = su2.Plan(N=N, batch=B, dtype="c64", algo=algo)
+    x = torch.empty(B * N ** 3, dtype=torch.complex64, device="cuda")
+    for b in range(B):
+        x[b * N ** 3:(b + 1) * N ** 3].copy_(torch.from_numpy(base[b % 4].reshape(-1)))
+    out = plan.forward(x)
+    plan.sync_status()
+    from oracle import grid as G
+    pairs = [(0, 0), (254, 254), (-254, 254), (255, -255), (1, 1), (-77, 129), (30, -2), (-201, -201), (3, 255)]
+    C = I.num_coeffs(N)
+    ref = {}
+    for gi in range(4):
+        f64 = base[gi].astype(np.complex128)
+        ref[gi] = {pq: T.forward_pair(f64, *pq) for pq in pairs}
+    for b in range(0, B, 7):
+        got = out[b * C:(b + 1) * C].cpu().numpy()
+        worst = scale = 0.0
+        for (n2, m2), (j0, vals) in ref[b % 4].items():
+            for i, v in enumerate(vals):
+                worst = max(worst, abs(got[G.coeff_index(j0 + 2 * i, m2, n2)] - v))
+                scale = max(scale, abs(v))
+        assert worst / scale < TOL32, (b, worst / scale)
