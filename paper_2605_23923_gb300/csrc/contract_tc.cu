@@ -11,18 +11,16 @@
 // x = x_hi + x_lo with x_hi = bf16(x), x_lo = bf16(x - x_hi) for both
 // operands, D += A_hi B_hi + A_hi B_lo + A_lo B_hi.
 //
-// A CTA (one per SM, persistent) owns 4 consecutive n at fixed (sector, m)
-// and 64 functions; per chunk of 16 nodes it
-//   * loads the F2 chunk [64 functions][16 nodes][4 n] with one 5-D TMA copy,
-//   * converts it to the BF16 hi/lo A operands (threads 0-127),
-//   * regenerates the d-values of the 4 pairs x 16 nodes by the three-term
-//     recurrence and writes the BF16 hi/lo B operands (threads 128-191),
-//   * issues 3 tcgen05.mma per pair from one thread, committed to an mbarrier
-//     that frees the stage two chunks later.
-// Two stages of every buffer overlap the MMAs and the next TMA with the
-// conversion and the recurrence.  The epilogue (warps 0-3 own the 128 TMEM
-// lanes) multiplies by i^{n-m} and writes 4 consecutive n of each coefficient
-// row with one contiguous store.
+// One persistent CTA per SM owns tiles of 4 consecutive n at fixed
+// (sector, m) and 64 functions.  Warp roles, connected by mbarriers:
+//   warp 0      TMA: F2 chunk [64 functions][16 nodes][4 n] into a staging ring
+//   warp 1      MMA issue (one thread), tensor-memory owner
+//   warps 2-5   convert staged F2 (fp32) to the BF16 hi/lo A operands
+//   warps 6-9   two generator groups (even / odd chunks): the d-values of the
+//               4 pairs x 16 nodes by the three-term recurrence, written as the
+//               BF16 hi/lo B operands
+//   warps 12-15 epilogue: tensor memory -> i^{n-m} * coefficients
+// Two stages of staging / A / B; the MMA commit of a stage frees it.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -37,43 +35,50 @@ namespace tc {
 constexpr int NP = 4;                       // pairs (consecutive n) per tile
 constexpr int KC = 16;                      // beta nodes per chunk = one MMA K step
 constexpr int BM = 64;                      // functions per tile (M = 128)
-constexpr int THREADS = 256;
+constexpr int NWARPS = 16;
+constexpr int THREADS = NWARPS * 32;
+constexpr int W_TMA = 0, W_MMA = 1, W_CONV = 2, N_CONV = 4, W_GEN = 6, W_EPI = 12;
 constexpr int RMAX = 128;                   // rows of l per pair (N <= 256)
-constexpr int STAGE_BYTES = BM * KC * NP * 8;       // F2 fp32 staging: 32 KB
-constexpr int OPB = 128 * KC * 2;                   // one bf16 operand of one pair: 4 KB
-constexpr int A_BYTES = 2 * NP * OPB;               // hi + lo, 4 pairs: 32 KB
-constexpr int B_BYTES = 2 * NP * OPB;               // 32 KB
-constexpr int OFF_STAGE = 0;
-constexpr int OFF_A = OFF_STAGE + 2 * STAGE_BYTES;
-constexpr int OFF_B = OFF_A + 2 * A_BYTES;
+constexpr int NMAX = 256;
+
+// Operand layouts (SWIZZLE_NONE canonical; core matrix = 8 rows x 16 bytes):
+// A, K-major:  (row, kk) -> (row/8)*SBO_A + (kk/8)*LBO_A + (row%8)*16 + (kk%8)*2
+// B, MN-major: (kk, col) -> (col/8)*SBO_B + (kk/8)*LBO_B + (kk%8)*16 + (col%8)*2
+// LBO_A = 144 (not 128) and a 32-byte skew between the pairs' A buffers keep
+// the converters' 4-byte stores free of bank conflicts.
+constexpr int LBO_A = 144, SBO_A = 288, LBO_B = 128, SBO_B = 256;
+constexpr int OPA = 16 * SBO_A + 32;        // one pair's A matrix (hi or lo), skewed
+constexpr int OPB = 16 * SBO_B;             // one pair's B matrix (hi or lo)
+constexpr int STAGE_BYTES = BM * KC * NP * 8;       // fp32 staging: 32 KB
+constexpr int A_BYTES = 2 * NP * OPA;
+constexpr int B_BYTES = 2 * NP * OPB;
+constexpr int OFF_STG = 0;
+constexpr int OFF_A = OFF_STG + 2 * STAGE_BYTES;
+constexpr int OFF_B = OFF_A + ((2 * A_BYTES + 127) / 128) * 128;
 constexpr int OFF_COEF = OFF_B + 2 * B_BYTES;
-constexpr int OFF_BAR = OFF_COEF + NP * RMAX * (int)sizeof(StepCoef<float>);
-constexpr int SMEM_BYTES = OFF_BAR + 8 * 8 + 16;
+constexpr int OFF_TAB = OFF_COEF + 2 * NP * RMAX * (int)sizeof(StepCoef<float>);
+constexpr int TAB_BYTES = NMAX * 8 * 3 + NMAX * 8;   // log2c, log2s, lf2 (double) + xsplit (float2)
+constexpr int OFF_BAR = OFF_TAB + TAB_BYTES;
+constexpr int NBAR = 12;
+constexpr int SMEM_BYTES = OFF_BAR + NBAR * 8 + 16;
+static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 constexpr uint32_t TMEM_COLS = 512;         // 4 pairs x 128 columns
 
-// Canonical SWIZZLE_NONE layouts (core matrix = 8 rows x 16 bytes):
-// A, K-major: element (row, kk) -> (row/8)*256 + (kk/8)*128 + (row%8)*16 + (kk%8)*2
-//             LBO (K step) = 128, SBO (M step) = 256.
-// B, MN-major: element (kk, col) -> (col/8)*256 + (kk/8)*128 + (kk%8)*16 + (col%8)*2
-//             LBO (K step) = 128, SBO (N step) = 256.
 __device__ __forceinline__ int a_off(int row, int kk) {
-    return (row >> 3) * 256 + (kk >> 3) * 128 + (row & 7) * 16 + (kk & 7) * 2;
-}
-__device__ __forceinline__ int b_off(int kk, int col) {
-    return (col >> 3) * 256 + (kk >> 3) * 128 + (kk & 7) * 16 + (col & 7) * 2;
+    return (row >> 3) * SBO_A + (kk >> 3) * LBO_A + (row & 7) * 16 + (kk & 7) * 2;
 }
 
-__device__ __forceinline__ uint64_t smem_desc(const void* p) {
+__device__ __forceinline__ uint64_t smem_desc(const void* p, uint32_t lbo, uint32_t sbo) {
     const uint32_t addr = smem_u32(p);
     uint64_t d = 0;
     d |= (uint64_t)((addr & 0x3FFFF) >> 4);
-    d |= (uint64_t)(128 >> 4) << 16;        // leading byte offset: K direction
-    d |= (uint64_t)(256 >> 4) << 32;        // stride byte offset: M / N direction
-    d |= (uint64_t)1 << 46;                 // descriptor version
-    return d;                               // base offset 0, no swizzle
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;    // leading byte offset: K direction
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;    // stride byte offset: M / N direction
+    d |= (uint64_t)1 << 46;                        // descriptor version
+    return d;                                      // base offset 0, no swizzle
 }
 
-// kind::f16 instruction descriptor: BF16 x BF16 -> F32, A K-major, B MN-major.
+// kind::f16 instruction descriptor: BF16 x BF16 -> F32, A K-major, B MN-major, M = 128.
 __device__ __forceinline__ uint32_t instr_desc(int nmma) {
     return (1u << 4) | (1u << 7) | (1u << 10) | (0u << 15) | (1u << 16) |
            ((uint32_t)(nmma >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
@@ -91,6 +96,12 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
 
 __device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4,
                                             uint64_t* bar) {
@@ -126,22 +137,43 @@ __global__ void __launch_bounds__(THREADS, 1)
 contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2* __restrict__ coeffs) {
     extern __shared__ __align__(1024) unsigned char smem[];
     constexpr int NCH = N / KC;
-    StepCoef<float>* coef = reinterpret_cast<StepCoef<float>*>(smem + OFF_COEF);
-    uint64_t* bar_full = reinterpret_cast<uint64_t*>(smem + OFF_BAR);        // [2] TMA landed
-    uint64_t* bar_mma = bar_full + 2;                                        // [2] MMAs of the stage done
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar_full + 8);
+    static_assert(NCH % 2 == 0, "even number of chunks: a generator group keeps its stage");
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OFF_BAR);
+    uint64_t* bar_full = bars + 0;     // [2] TMA landed                 (count 1 + tx)
+    uint64_t* bar_sfree = bars + 2;    // [2] staging consumed            (count N_CONV)
+    uint64_t* bar_afull = bars + 4;    // [2] A operands written          (count N_CONV)
+    uint64_t* bar_bfull = bars + 6;    // [2] B operands written          (count 2)
+    uint64_t* bar_opfree = bars + 8;   // [2] MMAs of the stage done      (tcgen05.commit)
+    uint64_t* bar_accfull = bars + 10; //     accumulators of a tile final (tcgen05.commit)
+    uint64_t* bar_accfree = bars + 11; //     epilogue drained TMEM        (count 4)
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + NBAR);
+    double* t_l2c = reinterpret_cast<double*>(smem + OFF_TAB);
+    double* t_l2s = t_l2c + NMAX;
+    double* t_lf2 = t_l2s + NMAX;
+    float2* t_xs = reinterpret_cast<float2*>(t_lf2 + NMAX);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    if (warp == 0) {
+    for (int t = tid; t < N; t += THREADS) {
+        t_l2c[t] = a.log2c[t];
+        t_l2s[t] = a.log2s[t];
+        t_lf2[t] = a.lf2[t];
+        t_xs[t] = a.xsplit[t];
+    }
+    if (warp == W_MMA) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      ::"r"(smem_u32(tslot)), "r"(TMEM_COLS) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init(&bar_full[0], 1);
-        mbar_init(&bar_full[1], 1);
-        mbar_init(&bar_mma[0], 1);
-        mbar_init(&bar_mma[1], 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&bar_full[i], 1);
+            mbar_init(&bar_sfree[i], N_CONV);
+            mbar_init(&bar_afull[i], N_CONV);
+            mbar_init(&bar_bfull[i], 2);
+            mbar_init(&bar_opfree[i], 1);
+        }
+        mbar_init(bar_accfull, 1);
+        mbar_init(bar_accfree, 4);
         mbar_fence_init();
     }
     tc_fence_before();
@@ -149,86 +181,155 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
     tc_fence_after();
     const uint32_t taddr = *tslot;
 
+    // seed tables in shared memory (generic pointers into this CTA's smem)
+    BandArgs as = a;
+    as.log2c = t_l2c;
+    as.log2s = t_l2s;
+    as.lf2 = t_lf2;
+    as.xsplit = t_xs;
+
     const int ntiles = 2 * N * (N / NP);
     const int nbb = (a.nfunc + BM - 1) / BM;
     const int nitems = ntiles * nbb;
-    uint32_t tma_iss[2] = {0u, 0u}, tma_got[2] = {0u, 0u};
-    uint32_t mma_iss[2] = {0u, 0u}, mma_got[2] = {0u, 0u};
 
-    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
-        const int t = item / nbb, bb = item % nbb;
-        Tile<NP> tl;
-        tl.decode(N, t);
-        if (!tl.any) continue;
-        const int Lt = tl.L;
-        const int nmma = (Lt + 15) & ~15;
-        const uint32_t idesc = instr_desc(nmma);
-
-        for (int idx = tid; idx < NP * (Lt - 1); idx += THREADS) {
-            const int p = idx % NP, r = idx / NP;
-            const int J = tl.j0 + 2 * r;
-            if (J >= tl.mu2[p]) coef[p * RMAX + r] = step_coef<float>(J, tl.n2[p], tl.m2);
-        }
-        fence_proxy_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-            for (int c = 0; c < 2 && c < NCH; ++c) {
-                mbar_arrive_expect_tx(&bar_full[c], (uint32_t)STAGE_BYTES);
-                tma_load_5d(smem + OFF_STAGE + c * STAGE_BYTES, &tmap, tl.nb * NP, tl.mi, tl.s, c * KC, bb * BM,
-                            &bar_full[c]);
+    if (warp == W_TMA) {
+        // ------------------------------------------------------------------ TMA
+        if (lane == 0) {
+            uint32_t g = 0;
+            for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+                Tile<NP> tl;
+                tl.decode(N, item / nbb);
+                if (!tl.any) continue;
+                const int bb = item % nbb;
+                for (int c = 0; c < NCH; ++c, ++g) {
+                    const int st = g & 1;
+                    const uint32_t u = g >> 1;
+                    if (u > 0) mbar_wait_bounded(&bar_sfree[st], (u - 1) & 1, a.err);
+                    mbar_arrive_expect_tx(&bar_full[st], (uint32_t)STAGE_BYTES);
+                    tma_load_5d(smem + OFF_STG + st * STAGE_BYTES, &tmap, tl.nb * NP, tl.mi, tl.s, c * KC, bb * BM,
+                                &bar_full[st]);
+                }
             }
         }
-        for (int c = 0; c < 2 && c < NCH; ++c) ++tma_iss[c];
-
-        for (int c = 0; c < NCH; ++c) {
-            const int st = c & 1;
-            if (mma_iss[st] > mma_got[st]) {         // stage operands still read by earlier MMAs
-                mbar_wait_bounded(&bar_mma[st], (mma_iss[st] - 1) & 1, a.err);
-                mma_got[st] = mma_iss[st];
-            }
-            mbar_wait_bounded(&bar_full[st], tma_got[st] & 1, a.err);
-            ++tma_got[st];
-            unsigned char* Ab = smem + OFF_A + st * A_BYTES;
-            unsigned char* Bb = smem + OFF_B + st * B_BYTES;
-            if (tid < 128) {
-                // ---- F2 (fp32) -> A_hi / A_lo, rows 2b (re) and 2b+1 (im), two nodes per item
-                const float2* stg = reinterpret_cast<const float2*>(smem + OFF_STAGE + st * STAGE_BYTES);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int i = tid + 128 * j;
-                    const int b = i >> 3, kp = i & 7;
-                    const float4* src = reinterpret_cast<const float4*>(stg + (b * KC + 2 * kp) * NP);
-                    const float4 q0 = src[0], q1 = src[1], q2 = src[2], q3 = src[3];
-                    // node 2kp: pairs (q0.xy, q0.zw, q1.xy, q1.zw); node 2kp+1: (q2.xy, q2.zw, q3.xy, q3.zw)
-                    const float re0[NP] = {q0.x, q0.z, q1.x, q1.z}, im0[NP] = {q0.y, q0.w, q1.y, q1.w};
-                    const float re1[NP] = {q2.x, q2.z, q3.x, q3.z}, im1[NP] = {q2.y, q2.w, q3.y, q3.w};
-                    const int ore = a_off(2 * b, 2 * kp), oim = a_off(2 * b + 1, 2 * kp);
+    } else if (warp == W_MMA) {
+        // ------------------------------------------------------------------ MMA
+        if (lane == 0) {
+            uint32_t g = 0, ti = 0;
+            for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+                Tile<NP> tl;
+                tl.decode(N, item / nbb);
+                if (!tl.any) continue;
+                const uint32_t idesc = instr_desc((tl.L + 15) & ~15);
+                if (ti > 0) mbar_wait_bounded(bar_accfree, (ti - 1) & 1, a.err);
+                tc_fence_after();
+                for (int c = 0; c < NCH; ++c, ++g) {
+                    const int st = g & 1;
+                    const uint32_t u = g >> 1;
+                    mbar_wait_bounded(&bar_afull[st], u & 1, a.err);
+                    mbar_wait_bounded(&bar_bfull[st], u & 1, a.err);
+                    tc_fence_after();
+                    unsigned char* Ab = smem + OFF_A + st * A_BYTES;
+                    unsigned char* Bb = smem + OFF_B + st * B_BYTES;
 #pragma unroll
                     for (int p = 0; p < NP; ++p) {
+                        if (!tl.valid[p]) continue;
+                        const uint32_t d = taddr + (uint32_t)(p * 128);
+                        const uint64_t ah = smem_desc(Ab + p * OPA, LBO_A, SBO_A);
+                        const uint64_t al = smem_desc(Ab + (NP + p) * OPA, LBO_A, SBO_A);
+                        const uint64_t bh = smem_desc(Bb + p * OPB, LBO_B, SBO_B);
+                        const uint64_t bl = smem_desc(Bb + (NP + p) * OPB, LBO_B, SBO_B);
+                        mma_bf16(d, ah, bh, idesc, c > 0);
+                        mma_bf16(d, ah, bl, idesc, true);
+                        mma_bf16(d, al, bh, idesc, true);
+                    }
+                    mma_commit(&bar_opfree[st]);
+                }
+                mma_commit(bar_accfull);
+                ++ti;
+            }
+        }
+    } else if (warp >= W_CONV && warp < W_CONV + N_CONV) {
+        // ------------------------------------------------------------------ F2 -> A (bf16 hi/lo)
+        // A warp takes 16 functions; per step it reads 32 consecutive staged
+        // complex values (node kk, pair p: lane = (kk % 8) * 4 + p) and lanes with
+        // even kk pack (kk, kk+1) into bf16x2 words.
+        const int cw = warp - W_CONV;
+        const int p = lane & 3, kl = lane >> 2;          // kl: node within the half-row
+        uint32_t g = 0;
+        for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+            Tile<NP> tl;
+            tl.decode(N, item / nbb);
+            if (!tl.any) continue;
+            for (int c = 0; c < NCH; ++c, ++g) {
+                const int st = g & 1;
+                const uint32_t u = g >> 1;
+                mbar_wait_bounded(&bar_full[st], u & 1, a.err);
+                if (u > 0) mbar_wait_bounded(&bar_opfree[st], (u - 1) & 1, a.err);
+                const float2* stg = reinterpret_cast<const float2*>(smem + OFF_STG + st * STAGE_BYTES);
+                unsigned char* Ab = smem + OFF_A + st * A_BYTES;
+                for (int it = 0; it < 32; ++it) {
+                    const int b = cw * 16 + (it >> 1);
+                    const int half = it & 1;                       // nodes 0-7 or 8-15
+                    const int kk = half * 8 + kl;
+                    const float2 v = stg[(b * KC + kk) * NP + p];
+                    const float re1 = __shfl_down_sync(0xffffffffu, v.x, 4);
+                    const float im1 = __shfl_down_sync(0xffffffffu, v.y, 4);
+                    if ((kl & 1) == 0) {
                         uint32_t hr, lr, hi_, li;
-                        split2(re0[p], re1[p], hr, lr);
-                        split2(im0[p], im1[p], hi_, li);
-                        *reinterpret_cast<uint32_t*>(Ab + p * OPB + ore) = hr;
-                        *reinterpret_cast<uint32_t*>(Ab + p * OPB + oim) = hi_;
-                        *reinterpret_cast<uint32_t*>(Ab + (NP + p) * OPB + ore) = lr;
-                        *reinterpret_cast<uint32_t*>(Ab + (NP + p) * OPB + oim) = li;
+                        split2(v.x, re1, hr, lr);
+                        split2(v.y, im1, hi_, li);
+                        const int ore = a_off(2 * b, kk), oim = a_off(2 * b + 1, kk);
+                        *reinterpret_cast<uint32_t*>(Ab + p * OPA + ore) = hr;
+                        *reinterpret_cast<uint32_t*>(Ab + p * OPA + oim) = hi_;
+                        *reinterpret_cast<uint32_t*>(Ab + (NP + p) * OPA + ore) = lr;
+                        *reinterpret_cast<uint32_t*>(Ab + (NP + p) * OPA + oim) = li;
                     }
                 }
-            } else if (tid < 128 + NP * KC) {
-                // ---- recurrence for (pair p, node k) -> B_hi / B_lo column kk
-                const int g = tid - 128, p = g >> 4, kk = g & 15, k = c * KC + kk;
-                unsigned char* Bh = Bb + p * OPB;
-                unsigned char* Bl = Bb + (NP + p) * OPB;
-                const int colbase = (kk >> 3) * 128 + (kk & 7) * 16;
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&bar_sfree[st]);
+                    mbar_arrive(&bar_afull[st]);
+                }
+            }
+        }
+    } else if (warp >= W_GEN && warp < W_GEN + 4) {
+        // ------------------------------------------------------------------ recurrence -> B (bf16 hi/lo)
+        const int grp = (warp - W_GEN) >> 1;               // handles the chunks of stage grp
+        const int gt = tid - W_GEN * 32 - grp * 64;        // 0..63
+        const int p = gt >> 4, kk = gt & 15;
+        StepCoef<float>* coef = reinterpret_cast<StepCoef<float>*>(smem + OFF_COEF) + grp * NP * RMAX;
+        uint32_t g = 0;
+        for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+            Tile<NP> tl;
+            tl.decode(N, item / nbb);
+            if (!tl.any) continue;
+            const int Lt = tl.L, nmma = (Lt + 15) & ~15;
+            named_sync(1 + grp, 64);                       // previous tile's coefficients no longer read
+            for (int idx = gt; idx < NP * (Lt - 1); idx += 64) {
+                const int pp = idx % NP, r = idx / NP;
+                const int J = tl.j0 + 2 * r;
+                if (J >= tl.mu2[pp]) coef[pp * RMAX + r] = step_coef<float>(J, tl.n2[pp], tl.m2);
+            }
+            named_sync(1 + grp, 64);
+            for (int c = 0; c < NCH; ++c, ++g) {
+                const int st = g & 1;
+                if (st != grp) continue;
+                const uint32_t u = g >> 1;
+                if (u > 0) mbar_wait_bounded(&bar_opfree[st], (u - 1) & 1, a.err);
+                unsigned char* Bh = smem + OFF_B + st * B_BYTES + p * OPB;
+                unsigned char* Bl = smem + OFF_B + st * B_BYTES + (NP + p) * OPB;
+                const int colbase = (kk >> 3) * LBO_B + (kk & 7) * 16;
                 if (!tl.valid[p]) {
                     for (int rb = 0; rb < nmma; rb += 8) {
-                        *reinterpret_cast<uint4*>(Bh + (rb >> 3) * 256 + colbase) = make_uint4(0, 0, 0, 0);
-                        *reinterpret_cast<uint4*>(Bl + (rb >> 3) * 256 + colbase) = make_uint4(0, 0, 0, 0);
+                        *reinterpret_cast<uint4*>(Bh + (rb >> 3) * SBO_B + colbase) = make_uint4(0, 0, 0, 0);
+                        *reinterpret_cast<uint4*>(Bl + (rb >> 3) * SBO_B + colbase) = make_uint4(0, 0, 0, 0);
                     }
                 } else {
                     Rec<float> rc;
-                    rc.seed(a, tl.n2[p], tl.m2, k);
+                    rc.seed(as, tl.n2[p], tl.m2, c * KC + kk);
                     const int rp = (tl.mu2[p] - tl.j0) / 2;
+                    const StepCoef<float>* cp = coef + p * RMAX;
                     for (int rb = 0; rb < nmma; rb += 8) {
                         float v[8];
 #pragma unroll
@@ -238,7 +339,7 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
                                 v[i] = 0.f;
                             } else {
                                 v[i] = rc.value();
-                                if (r + 1 < Lt) rc.step(coef[p * RMAX + r]);
+                                if (r + 1 < Lt) rc.step(cp[r]);
                             }
                         }
                         uint4 h, l;
@@ -246,87 +347,69 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
                         split2(v[2], v[3], h.y, l.y);
                         split2(v[4], v[5], h.z, l.z);
                         split2(v[6], v[7], h.w, l.w);
-                        *reinterpret_cast<uint4*>(Bh + (rb >> 3) * 256 + colbase) = h;
-                        *reinterpret_cast<uint4*>(Bl + (rb >> 3) * 256 + colbase) = l;
+                        *reinterpret_cast<uint4*>(Bh + (rb >> 3) * SBO_B + colbase) = h;
+                        *reinterpret_cast<uint4*>(Bl + (rb >> 3) * SBO_B + colbase) = l;
                     }
                 }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bar_bfull[st]);
             }
-            fence_proxy_async_smem();
-            tc_fence_before();
-            __syncthreads();
-            if (tid == 0 && c + 2 < NCH) {
-                mbar_arrive_expect_tx(&bar_full[st], (uint32_t)STAGE_BYTES);
-                tma_load_5d(smem + OFF_STAGE + st * STAGE_BYTES, &tmap, tl.nb * NP, tl.mi, tl.s, (c + 2) * KC,
-                            bb * BM, &bar_full[st]);
-            }
-            if (c + 2 < NCH) ++tma_iss[st];
-            if (tid == 32) {
-                tc_fence_after();
-#pragma unroll
-                for (int p = 0; p < NP; ++p) {
-                    if (!tl.valid[p]) continue;
-                    const uint32_t d = taddr + (uint32_t)(p * 128);
-                    const uint64_t ah = smem_desc(Ab + p * OPB), al = smem_desc(Ab + (NP + p) * OPB);
-                    const uint64_t bh = smem_desc(Bb + p * OPB), bl = smem_desc(Bb + (NP + p) * OPB);
-                    mma_bf16(d, ah, bh, idesc, c > 0);
-                    mma_bf16(d, ah, bl, idesc, true);
-                    mma_bf16(d, al, bh, idesc, true);
-                }
-                mma_commit(&bar_mma[st]);
-            }
-            ++mma_iss[st];
         }
-
-        // ---- epilogue: TMEM -> coefficients
-        {
-            const int st = (NCH - 1) & 1;
-            mbar_wait_bounded(&bar_mma[st], (mma_iss[st] - 1) & 1, a.err);
-            mma_got[st] = mma_iss[st];
-        }
-        tc_fence_after();
-        if (warp < 4) {
-            const int row = 32 * warp + lane;
+    } else if (warp >= W_EPI && warp < W_EPI + 4) {
+        // ------------------------------------------------------------------ epilogue
+        const int q = warp - W_EPI;                          // TMEM lane quadrant (warp % 4)
+        const int row = 32 * q + lane;
+        const bool even = (row & 1) == 0;
+        uint32_t ti = 0;
+        for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+            Tile<NP> tl;
+            tl.decode(N, item / nbb);
+            if (!tl.any) continue;
+            const int bb = item % nbb;
+            const int Lt = tl.L, nmma = (Lt + 15) & ~15;
+            mbar_wait_bounded(bar_accfull, ti & 1, a.err);
+            tc_fence_after();
             const int fb = bb * BM + (row >> 1);
             const bool fok = fb < a.nfunc;
             const int f = fok ? a.fidx[fb] : 0;
             float2* cf = coeffs + (fok ? a.coeff_off[f] : 0);
-            const bool even = (row & 1) == 0;
             for (int cc = 0; cc < nmma; cc += 16) {
                 uint32_t rv[NP][16];
 #pragma unroll
-                for (int p = 0; p < NP; ++p)
-                    tmem_ld16(taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)(p * 128 + cc), rv[p]);
+                for (int pp = 0; pp < NP; ++pp)
+                    tmem_ld16(taddr + ((uint32_t)(32 * q) << 16) + (uint32_t)(pp * 128 + cc), rv[pp]);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int r = cc + j;
                     float mine[NP], other[NP];
 #pragma unroll
-                    for (int p = 0; p < NP; ++p) {
-                        mine[p] = __uint_as_float(rv[p][j]);
-                        other[p] = __shfl_xor_sync(0xffffffffu, mine[p], 1);
+                    for (int pp = 0; pp < NP; ++pp) {
+                        mine[pp] = __uint_as_float(rv[pp][j]);
+                        other[pp] = __shfl_xor_sync(0xffffffffu, mine[pp], 1);
                     }
                     if (r >= Lt || !even || !fok) continue;
                     const int J = tl.j0 + 2 * r;
                     const size_t rowbase = block_offset(J) + (size_t)((tl.m2 + J) / 2) * (J + 1);
 #pragma unroll
-                    for (int p = 0; p < NP; ++p) {
-                        if (!tl.valid[p] || J < tl.mu2[p]) continue;
-                        const float2 z = cmul_ipow(make_float2(mine[p], other[p]), (tl.n2[p] - tl.m2) / 2);
-                        cf[rowbase + (tl.n2[p] + J) / 2] = z;
+                    for (int pp = 0; pp < NP; ++pp) {
+                        if (!tl.valid[pp] || J < tl.mu2[pp]) continue;
+                        cf[rowbase + (tl.n2[pp] + J) / 2] =
+                            cmul_ipow(make_float2(mine[pp], other[pp]), (tl.n2[pp] - tl.m2) / 2);
                     }
                 }
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_accfree);
+            ++ti;
         }
-        tc_fence_before();
-        __syncthreads();
     }
-    // drain: the last commit of the other stage may still be outstanding
-    for (int st = 0; st < 2; ++st)
-        if (mma_iss[st] > mma_got[st]) mbar_wait_bounded(&bar_mma[st], (mma_iss[st] - 1) & 1, a.err);
-    tc_fence_after();
+    tc_fence_before();
     __syncthreads();
-    if (warp == 0)
+    tc_fence_after();
+    if (warp == W_MMA)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TMEM_COLS) : "memory");
 }
 
