@@ -182,6 +182,11 @@ su2::BandArgs band_args(const su2_plan_s* P, const Band& b) {
     a.twist64 = b.d_twist64;
     a.err = P->d_err;
     a.ws_group_off = b.fids.empty() ? 0 : P->ws_off[b.fids[0]];
+    a.grid_group_off = b.fids.empty() ? 0 : P->grid_off[b.fids[0]];
+    a.grid_regular = 1;
+    const size_t n3 = (size_t)b.N * b.N * b.N;
+    for (size_t i = 0; i < b.fids.size(); ++i)
+        if (P->grid_off[b.fids[i]] != a.grid_group_off + i * n3) a.grid_regular = 0;
     return a;
 }
 

@@ -300,6 +300,10 @@ struct BandArgs {
     const double2* twist64;
     int* err;                     // device error word
     size_t ws_group_off;          // stage-1 plane offset of the group's first function
+                                  // (a group's planes are contiguous: function i of
+                                  // the group at ws_group_off + i * 2 N^3)
+    size_t grid_group_off;        // grid offset of the group's first function
+    int grid_regular;             // 1: function i of the group at grid_group_off + i * N^3
 };
 
 }  // namespace su2

@@ -431,19 +431,13 @@ static EncodeTiledFn encode_fn() {
 
 template <int N>
 static cudaError_t launch_n(const BandArgs& a, const void* ws, void* coeffs, cudaStream_t st) {
-    EncodeTiledFn enc = encode_fn();
-    if (!enc) return cudaErrorNotSupported;
     CUtensorMap map;
     const cuuint64_t dims[5] = {(cuuint64_t)N, (cuuint64_t)N, 2, (cuuint64_t)N, (cuuint64_t)a.nfunc};
     const cuuint64_t strides[4] = {(cuuint64_t)N * 8, (cuuint64_t)N * N * 8, (cuuint64_t)2 * N * N * 8,
                                    (cuuint64_t)2 * N * N * N * 8};
     const cuuint32_t box[5] = {NP, 1, 1, KC, BM};
-    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-    void* base = (void*)((const char*)ws + a.ws_group_off * sizeof(float2));
-    CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5, base, dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    const void* base = (const char*)ws + a.ws_group_off * sizeof(float2);
+    if (!encode_tensor_map_8b(&map, 5, base, dims, strides, box)) return cudaErrorNotSupported;
     auto kern = contract_tc_kernel<N>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
@@ -457,6 +451,17 @@ static cudaError_t launch_n(const BandArgs& a, const void* ws, void* coeffs, cud
 }
 
 }  // namespace tc
+
+bool encode_tensor_map_8b(CUtensorMap* map, int rank, const void* base, const cuuint64_t* dims,
+                          const cuuint64_t* strides_bytes, const cuuint32_t* box) {
+    tc::EncodeTiledFn enc = tc::encode_fn();
+    if (!enc) return false;
+    cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, (cuuint32_t)rank, const_cast<void*>(base), dims,
+                     strides_bytes, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
 
 bool tc_supported(int N) { return N == 64 || N == 128 || N == 256; }
 

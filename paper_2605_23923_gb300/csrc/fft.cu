@@ -22,6 +22,8 @@
 // After a cluster barrier, CTA c' gathers the rows p in [32c', 32c'+32) from
 // every CTA's shared memory (ld.shared::cluster) and runs the row DFTs over
 // j2; the second half of that DFT writes 32 consecutive n per warp store.
+#include <string.h>
+
 #include "common.cuh"
 #include "su2_internal.h"
 
@@ -341,18 +343,21 @@ fft_fwd_pipe(BandArgs a, const float2* __restrict__ grid, float2* __restrict__ w
 // complex64).  Work items are (function, beta node, sector); one cluster of
 // C = N/16 CTAs takes items q, q + nq, ...  CTA c holds the 16 columns
 // j2 in [16c, 16c+16) of the item's N x N plane:
-//   S[2]  column slabs, filled by 1-D bulk copies (TMA) one item ahead;
-//   1A/1B column DFTs over j1 in place in S;
-//   push  every row p of the result goes, as one 128-byte bulk copy between
-//         shared memories, to the CTA owning p (c' = p/16), completion counted
-//         on that CTA's mbarrier;
-//   R     the received 16 rows (all N columns); 2A/2B row DFTs over j2, the
-//         2A result written back with an XOR swizzle so that 2B reads one
-//         column across 16 rows without bank conflicts; 2B stores F2 rows.
+//   S[2]  column slabs [j1][16], filled one item ahead by TMA (one 3-D tensor
+//         copy when the group's grids are regularly strided, else one bulk
+//         copy per row);
+//   1A    column DFT over j1, stride-R1 part, in place;
+//   1B    R1-point DFTs; bin p is written to row p (natural order), so the 16
+//         rows owned by CTA c' = p/16 form one contiguous 2 KB block;
+//   push  one 2 KB bulk copy (shared -> shared) per destination CTA into its
+//         receive buffer R[source][16 rows][16 columns], completion counted
+//         on the destination's mbarrier;
+//   2A/2B row DFTs over j2 (2A result written back XOR-swizzled so that 2B
+//         reads one column across 16 rows without bank conflicts); 2B stores
+//         16 consecutive n per half-warp.
 // One cluster barrier per item, split: arrive after 2B (my R is free and I
-// have received the item, so every sender's slab is free), wait after the
-// next item's column passes (before pushing into other CTAs' R and before
-// refilling the slab the previous push read).
+// have received the item, so every sender's slab is free), wait before the
+// next push and the next slab refill.
 // ---------------------------------------------------------------------------
 template <int N>
 struct XCfg {
@@ -361,22 +366,32 @@ struct XCfg {
     static constexpr int R1 = Radix<N>::R1, R2 = Radix<N>::R2;
     static constexpr int THREADS = 256;
     static constexpr int SLAB = N * W;                      // float2 per slab
-    static constexpr int F2S = 2 * SLAB + W * N + N + 2 * N;
+    static constexpr int F2S = 2 * SLAB + W * N + N + 2 * N + N / 2;
     static constexpr size_t smem_bytes() { return (size_t)F2S * sizeof(float2) + 3 * sizeof(uint64_t); }
 };
 
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar)) : "memory");
+}
+
 template <int N>
 __global__ void __launch_bounds__(256, 2)
-fft_fwd_xchg(BandArgs a, const float2* __restrict__ grid, float2* __restrict__ ws) {
+fft_fwd_xchg(BandArgs a, const __grid_constant__ CUtensorMap gmap, const float2* __restrict__ grid,
+             float2* __restrict__ ws) {
     using P = XCfg<N>;
     constexpr int C = P::C, W = P::W, R1 = P::R1, R2 = P::R2, THREADS = P::THREADS, SLAB = P::SLAB;
     static_assert(C >= 2 && C <= 16, "cluster size");
+    static_assert(W * R2 <= THREADS && W * R1 <= THREADS, "one task per thread");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float2* S = reinterpret_cast<float2*>(smem_raw);       // [2][N][W]
-    float2* R = S + 2 * SLAB;                               // [W][N] (swizzled after 2A)
+    float2* R = S + 2 * SLAB;                               // [C][W][W] received, then [W][N] swizzled
     float2* om = R + W * N;                                 // exp(+2 pi i t/N)
     float2* tw2 = om + N;                                   // exp(i pi t/N), t < 2N
-    uint64_t* mbS = reinterpret_cast<uint64_t*>(tw2 + 2 * N);   // [2]
+    float* wk = reinterpret_cast<float*>(tw2 + 2 * N);      // beta weights
+    uint64_t* mbS = reinterpret_cast<uint64_t*>(tw2 + 2 * N + N / 2);   // [2]
     uint64_t* mbR = mbS + 2;
 
     const int c = (int)cluster_ctarank();
@@ -384,7 +399,10 @@ fft_fwd_xchg(BandArgs a, const float2* __restrict__ grid, float2* __restrict__ w
     const int nitems = a.nfunc * N * 2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-    for (int t = tid; t < N; t += THREADS) om[t] = a.om32[t];
+    for (int t = tid; t < N; t += THREADS) {
+        om[t] = a.om32[t];
+        wk[t] = a.w32[t];
+    }
     for (int t = tid; t < 2 * N; t += THREADS) {
         const float2 z = a.twist32[t & (N - 1)];
         tw2[t] = (t < N) ? z : make_float2(-z.x, -z.y);
@@ -402,13 +420,21 @@ fft_fwd_xchg(BandArgs a, const float2* __restrict__ grid, float2* __restrict__ w
 
     auto load_slab = [&](int item, int buf) {      // warp 0
         const int plane = item >> 1;
-        const int f = a.fidx[plane / N], k = plane % N;
-        const float2* src = grid + a.grid_off[f] + (size_t)k * N + c * W;
+        const int fb = plane / N, k = plane % N;
         float2* dst = S + buf * SLAB;
-        if (lane == 0) mbar_arrive_expect_tx(&mbS[buf], (uint32_t)(SLAB * sizeof(float2)));
-        __syncwarp();
-        for (int j1 = lane; j1 < N; j1 += 32)
-            bulk_g2s(dst + j1 * W, src + (size_t)j1 * N * N, (uint32_t)(W * sizeof(float2)), &mbS[buf]);
+        if (a.grid_regular) {
+            if (lane == 0) {
+                mbar_arrive_expect_tx(&mbS[buf], (uint32_t)(SLAB * sizeof(float2)));
+                tma_load_3d(dst, &gmap, c * W, k, fb * N, &mbS[buf]);
+            }
+        } else {
+            const int f = a.fidx[fb];
+            const float2* src = grid + a.grid_off[f] + (size_t)k * N + c * W;
+            if (lane == 0) mbar_arrive_expect_tx(&mbS[buf], (uint32_t)(SLAB * sizeof(float2)));
+            __syncwarp();
+            for (int j1 = lane; j1 < N; j1 += 32)
+                bulk_g2s(dst + j1 * W, src + (size_t)j1 * N * N, (uint32_t)(W * sizeof(float2)), &mbS[buf]);
+        }
     };
 
     if (q < nitems && warp == 0) load_slab(q, 0);
@@ -416,14 +442,13 @@ fft_fwd_xchg(BandArgs a, const float2* __restrict__ grid, float2* __restrict__ w
     for (int item = q; item < nitems; item += nq, ++it) {
         const int buf = it & 1;
         const int s = item & 1, plane = item >> 1;
-        const int f = a.fidx[plane / N], k = plane % N;
+        const int fb = plane / N, k = plane % N;
         float2* Sb = S + buf * SLAB;
         mbar_wait_bounded(&mbS[buf], (uint32_t)((it >> 1) & 1), a.err);
 
         // Pass 1A: column DFT over j1, stride-R1 part, in place (sector 1 pre-twisted).
-#pragma unroll
-        for (int task = tid; task < W * R1; task += THREADS) {
-            const int jc = task % W, ia = task / W;
+        if (tid < W * R1) {
+            const int jc = tid % W, ia = tid / W;
             const int j2 = c * W + jc;
             float2 v[R2];
 #pragma unroll
@@ -438,16 +463,20 @@ fft_fwd_xchg(BandArgs a, const float2* __restrict__ grid, float2* __restrict__ w
                 Sb[(ia + R1 * qb) * W + jc] = (qb == 0) ? v[0] : cmul(v[qb], om[ia * qb]);
         }
         __syncthreads();
-        // Pass 1B: R1-point DFTs in place; bin p = qb + R2*qa sits in row qa + R1*qb.
-#pragma unroll
-        for (int task = tid; task < W * R2; task += THREADS) {
-            const int jc = task % W, qb = task / W;
+        // Pass 1B: R1-point DFTs; bin p = qb + R2*qa goes to row p.
+        {
             float2 v[R1];
+            const int jc = tid % W, qb = tid / W;
+            if (tid < W * R2) {
 #pragma unroll
-            for (int ia = 0; ia < R1; ++ia) v[ia] = Sb[(ia + R1 * qb) * W + jc];
-            dft_reg<R1, 1, float>(v);
+                for (int ia = 0; ia < R1; ++ia) v[ia] = Sb[(ia + R1 * qb) * W + jc];
+                dft_reg<R1, 1, float>(v);
+            }
+            __syncthreads();
+            if (tid < W * R2) {
 #pragma unroll
-            for (int qa = 0; qa < R1; ++qa) Sb[(qa + R1 * qb) * W + jc] = v[qa];
+                for (int qa = 0; qa < R1; ++qa) Sb[(qb + R2 * qa) * W + jc] = v[qa];
+            }
         }
         fence_proxy_async_smem();
         __syncthreads();
@@ -459,49 +488,42 @@ fft_fwd_xchg(BandArgs a, const float2* __restrict__ grid, float2* __restrict__ w
                 load_slab(next, buf ^ 1);
             }
         } else if (warp == 1) {
-            // push row p (storage row p/R2 + R1*(p%R2)) to CTA p/W, row p%W, columns [cW, cW+W)
             if (lane == 0) mbar_arrive_expect_tx(mbR, (uint32_t)(W * N * sizeof(float2)));
-            for (int p = lane; p < N; p += 32) {
-                const int row = p / R2 + R1 * (p % R2);
-                bulk_s2s_remote(R + (p % W) * N + c * W, Sb + row * W, (uint32_t)(W * sizeof(float2)), mbR,
-                                (unsigned)(p / W));
-            }
+            __syncwarp();
+            if (lane < C)   // rows [16*lane, 16*lane + 16) to CTA `lane`, block `c` of its R
+                bulk_s2s_remote(R + c * W * W, Sb + lane * W * W, (uint32_t)(W * W * sizeof(float2)), mbR,
+                                (unsigned)lane);
         }
         mbar_wait_bounded(mbR, (uint32_t)(it & 1), a.err);
 
         // Pass 2A: row DFT over j2, stride-R1 part; lanes run along the row.
-        constexpr int NT2 = (W * R1 + THREADS - 1) / THREADS;
-        float2 hold[NT2][R2];
+        {
+            float2 v[R2];
+            const int ia = tid % R1, pl = tid / R1;
+            if (tid < W * R1) {
 #pragma unroll
-        for (int i2 = 0; i2 < NT2; ++i2) {
-            const int task = tid + i2 * THREADS;
-            if (task < W * R1) {
-                const int ia = task % R1, pl = task / R1;
-                float2 v[R2];
-#pragma unroll
-                for (int b = 0; b < R2; ++b) v[b] = R[pl * N + ia + R1 * b];
+                for (int b = 0; b < R2; ++b) {
+                    const int j2 = ia + R1 * b;
+                    v[b] = R[(j2 / W) * W * W + pl * W + (j2 % W)];
+                }
                 dft_reg<R2, 1, float>(v);
 #pragma unroll
-                for (int qb = 0; qb < R2; ++qb) hold[i2][qb] = (qb == 0) ? v[0] : cmul(v[qb], om[ia * qb]);
+                for (int qb = 1; qb < R2; ++qb) v[qb] = cmul(v[qb], om[ia * qb]);
             }
-        }
-        __syncthreads();
+            __syncthreads();
+            if (tid < W * R1) {
 #pragma unroll
-        for (int i2 = 0; i2 < NT2; ++i2) {
-            const int task = tid + i2 * THREADS;
-            if (task < W * R1) {
-                const int ia = task % R1, pl = task / R1;
-#pragma unroll
-                for (int qb = 0; qb < R2; ++qb) R[pl * N + ((ia + R1 * qb) ^ (pl & 15))] = hold[i2][qb];
+                for (int qb = 0; qb < R2; ++qb) R[pl * N + ((ia + R1 * qb) ^ (pl & 15))] = v[qb];
             }
         }
         __syncthreads();
         // Pass 2B: R1-point DFTs, scale, sign, store F2 (16 consecutive n per half-warp).
-        const float scale = a.w32[k] / (2.f * (float)N * (float)N);
-        float2* out = ws + a.ws_off[f] + ((size_t)k * 2 + s) * N * N;
-#pragma unroll
-        for (int task = tid; task < W * R2; task += THREADS) {
-            const int pl = task % W, qb = task / W;
+        if (tid < W * R2) {
+            const float scale = wk[k] / (2.f * (float)N * (float)N);
+            const size_t plane_off = a.grid_regular ? a.ws_group_off + (size_t)fb * 2 * N * N * N
+                                                    : a.ws_off[a.fidx[fb]];
+            float2* out = ws + plane_off + ((size_t)k * 2 + s) * N * N;
+            const int pl = tid % W, qb = tid / W;
             const int p = c * W + pl;
             float2 v[R1];
 #pragma unroll
@@ -842,7 +864,18 @@ static cudaError_t launch_xchg(const BandArgs& a, const void* in, void* out, cud
     const int nitems = a.nfunc * N * 2;
     const int ncl = nitems < max_clusters ? nitems : max_clusters;
     cfg.gridDim = dim3(P::C * ncl, 1, 1);
-    return cudaLaunchKernelEx(&cfg, kern, a, (const float2*)in, (float2*)out);
+    CUtensorMap gmap;
+    memset(&gmap, 0, sizeof(gmap));
+    BandArgs b = a;
+    if (b.grid_regular) {
+        // rows (function, j1) x beta nodes k x gamma nodes j2 of the group's grids
+        const cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)a.nfunc * N};
+        const cuuint64_t strides[2] = {(cuuint64_t)N * 8, (cuuint64_t)N * N * 8};
+        const cuuint32_t box[3] = {(cuuint32_t)P::W, 1, (cuuint32_t)N};
+        const void* base = (const float2*)in + a.grid_group_off;
+        if (!encode_tensor_map_8b(&gmap, 3, base, dims, strides, box)) b.grid_regular = 0;
+    }
+    return cudaLaunchKernelEx(&cfg, kern, b, gmap, (const float2*)in, (float2*)out);
 }
 
 template <typename T, bool FWD>

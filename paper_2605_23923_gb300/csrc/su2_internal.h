@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <cuda.h>
+
 #include "common.cuh"
 
 namespace su2 {
@@ -23,5 +25,10 @@ cudaError_t launch_contract_transpose(const BandArgs& a, bool fp64, TransposeMod
 // Stage 2 on tensor cores (split-BF16 operands, FP32 accumulation).
 cudaError_t launch_contract_forward_tc(const BandArgs& a, const void* ws, void* coeffs, cudaStream_t st);
 bool tc_supported(int N);
+
+// Encodes a tiled TMA descriptor over 8-byte elements (no swizzle, zero fill);
+// false if the driver entry point is unavailable or the arguments are rejected.
+bool encode_tensor_map_8b(CUtensorMap* map, int rank, const void* base, const cuuint64_t* dims,
+                          const cuuint64_t* strides_bytes, const cuuint32_t* box);
 
 }  // namespace su2
