@@ -15,7 +15,7 @@
 // (sector, m) and 64 functions.  Warp roles, connected by mbarriers:
 //   warp 0      TMA: F2 chunk [64 functions][16 nodes][4 n] into a staging ring
 //   warp 1      MMA issue (one thread), tensor-memory owner
-//   warps 2-5   convert staged F2 (fp32) to the BF16 hi/lo A operands
+//   warps 2-5, 10-11  convert staged F2 (fp32) to the BF16 hi/lo A operands
 //   warps 6-9   two generator groups (even / odd chunks): the d-values of the
 //               4 pairs x 16 nodes by the three-term recurrence, written as the
 //               BF16 hi/lo B operands
@@ -37,7 +37,8 @@ constexpr int KC = 16;                      // beta nodes per chunk = one MMA K 
 constexpr int BM = 64;                      // functions per tile (M = 128)
 constexpr int NWARPS = 16;
 constexpr int THREADS = NWARPS * 32;
-constexpr int W_TMA = 0, W_MMA = 1, W_CONV = 2, N_CONV = 4, W_GEN = 6, W_EPI = 12;
+constexpr int W_TMA = 0, W_MMA = 1, W_CONV = 2, W_GEN = 6, W_CONV2 = 10, W_EPI = 12;
+constexpr int N_CONV = 6;                   // converter warps: 2-5 and 10-11
 constexpr int RMAX = 128;                   // rows of l per pair (N <= 256)
 constexpr int NMAX = 256;
 
@@ -248,13 +249,12 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
                 ++ti;
             }
         }
-    } else if (warp >= W_CONV && warp < W_CONV + N_CONV) {
+    } else if ((warp >= W_CONV && warp < W_CONV + 4) || warp == W_CONV2 || warp == W_CONV2 + 1) {
         // ------------------------------------------------------------------ F2 -> A (bf16 hi/lo)
-        // A warp takes 16 functions; per step it reads 32 consecutive staged
-        // complex values (node kk, pair p: lane = (kk % 8) * 4 + p) and lanes with
-        // even kk pack (kk, kk+1) into bf16x2 words.
-        const int cw = warp - W_CONV;
-        const int p = lane & 3, kl = lane >> 2;          // kl: node within the half-row
+        // Item = (function b, node pair kp, pair p): two staged values (nodes 2kp,
+        // 2kp+1) -> one bf16x2 word per row (re: 2b, im: 2b+1) for hi and lo.
+        const int cw = (warp < W_CONV + 4) ? warp - W_CONV : 4 + (warp - W_CONV2);
+        const int ct = cw * 32 + lane;                     // 0 .. 191
         uint32_t g = 0;
         for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
             Tile<NP> tl;
@@ -267,23 +267,18 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
                 if (u > 0) mbar_wait_bounded(&bar_opfree[st], (u - 1) & 1, a.err);
                 const float2* stg = reinterpret_cast<const float2*>(smem + OFF_STG + st * STAGE_BYTES);
                 unsigned char* Ab = smem + OFF_A + st * A_BYTES;
-                for (int it = 0; it < 32; ++it) {
-                    const int b = cw * 16 + (it >> 1);
-                    const int half = it & 1;                       // nodes 0-7 or 8-15
-                    const int kk = half * 8 + kl;
-                    const float2 v = stg[(b * KC + kk) * NP + p];
-                    const float re1 = __shfl_down_sync(0xffffffffu, v.x, 4);
-                    const float im1 = __shfl_down_sync(0xffffffffu, v.y, 4);
-                    if ((kl & 1) == 0) {
-                        uint32_t hr, lr, hi_, li;
-                        split2(v.x, re1, hr, lr);
-                        split2(v.y, im1, hi_, li);
-                        const int ore = a_off(2 * b, kk), oim = a_off(2 * b + 1, kk);
-                        *reinterpret_cast<uint32_t*>(Ab + p * OPA + ore) = hr;
-                        *reinterpret_cast<uint32_t*>(Ab + p * OPA + oim) = hi_;
-                        *reinterpret_cast<uint32_t*>(Ab + (NP + p) * OPA + ore) = lr;
-                        *reinterpret_cast<uint32_t*>(Ab + (NP + p) * OPA + oim) = li;
-                    }
+                for (int i = ct; i < BM * (KC / 2) * NP; i += 32 * N_CONV) {
+                    const int p = i & 3, kp = (i >> 2) & 7, b = i >> 5;
+                    const float2 v0 = stg[(b * KC + 2 * kp) * NP + p];
+                    const float2 v1 = stg[(b * KC + 2 * kp + 1) * NP + p];
+                    uint32_t hr, lr, hi_, li;
+                    split2(v0.x, v1.x, hr, lr);
+                    split2(v0.y, v1.y, hi_, li);
+                    const int ore = a_off(2 * b, 2 * kp), oim = a_off(2 * b + 1, 2 * kp);
+                    *reinterpret_cast<uint32_t*>(Ab + p * OPA + ore) = hr;
+                    *reinterpret_cast<uint32_t*>(Ab + p * OPA + oim) = hi_;
+                    *reinterpret_cast<uint32_t*>(Ab + (NP + p) * OPA + ore) = lr;
+                    *reinterpret_cast<uint32_t*>(Ab + (NP + p) * OPA + oim) = li;
                 }
                 fence_proxy_async_smem();
                 __syncwarp();
@@ -359,8 +354,6 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
     } else if (warp >= W_EPI && warp < W_EPI + 4) {
         // ------------------------------------------------------------------ epilogue
         const int q = warp - W_EPI;                          // TMEM lane quadrant (warp % 4)
-        const int row = 32 * q + lane;
-        const bool even = (row & 1) == 0;
         uint32_t ti = 0;
         for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
             Tile<NP> tl;
@@ -370,10 +363,21 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
             const int Lt = tl.L, nmma = (Lt + 15) & ~15;
             mbar_wait_bounded(bar_accfull, ti & 1, a.err);
             tc_fence_after();
-            const int fb = bb * BM + (row >> 1);
-            const bool fok = fb < a.nfunc;
-            const int f = fok ? a.fidx[fb] : 0;
-            float2* cf = coeffs + (fok ? a.coeff_off[f] : 0);
+            // After the TMEM load lane l holds row 32q + l (function 16q + l/2, re or im)
+            // for the 4 pairs.  For the stores, lane t takes function 16q + 8h + t/4 and
+            // pair t%4 (h = 0, 1), so 4 adjacent lanes write 4 consecutive n.
+            const int pt = lane & 3;
+            float2* cfh[2];
+            bool okh[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int fb = bb * BM + 16 * q + 8 * h + (lane >> 2);
+                okh[h] = fb < a.nfunc;
+                cfh[h] = coeffs + (okh[h] ? a.coeff_off[a.fidx[fb]] : 0);
+            }
+            const int n2t = tl.n2[pt], mu2t = tl.mu2[pt];
+            const bool vt = tl.valid[pt];
+            const int ipw = (n2t - tl.m2) / 2;
             for (int cc = 0; cc < nmma; cc += 16) {
                 uint32_t rv[NP][16];
 #pragma unroll
@@ -383,20 +387,20 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int r = cc + j;
-                    float mine[NP], other[NP];
-#pragma unroll
-                    for (int pp = 0; pp < NP; ++pp) {
-                        mine[pp] = __uint_as_float(rv[pp][j]);
-                        other[pp] = __shfl_xor_sync(0xffffffffu, mine[pp], 1);
-                    }
-                    if (r >= Lt || !even || !fok) continue;
                     const int J = tl.j0 + 2 * r;
                     const size_t rowbase = block_offset(J) + (size_t)((tl.m2 + J) / 2) * (J + 1);
 #pragma unroll
-                    for (int pp = 0; pp < NP; ++pp) {
-                        if (!tl.valid[pp] || J < tl.mu2[pp]) continue;
-                        cf[rowbase + (tl.n2[pp] + J) / 2] =
-                            cmul_ipow(make_float2(mine[pp], other[pp]), (tl.n2[pp] - tl.m2) / 2);
+                    for (int h = 0; h < 2; ++h) {
+                        const int src = 16 * h + 2 * (lane >> 2);      // lane holding re of my function
+                        float re = 0.f, im = 0.f;
+#pragma unroll
+                        for (int pp = 0; pp < NP; ++pp) {
+                            const float vr = __shfl_sync(0xffffffffu, __uint_as_float(rv[pp][j]), src);
+                            const float vi = __shfl_sync(0xffffffffu, __uint_as_float(rv[pp][j]), src + 1);
+                            if (pp == pt) { re = vr; im = vi; }
+                        }
+                        if (r < Lt && okh[h] && vt && J >= mu2t)
+                            cfh[h][rowbase + (n2t + J) / 2] = cmul_ipow(make_float2(re, im), ipw);
                     }
                 }
             }
