@@ -141,6 +141,25 @@ su2_status su2_inverse(su2_plan_t plan, const void* coeffs, void* grid, void* ws
 su2_status su2_backward(su2_plan_t plan, const void* grad_coeffs, void* grad_grid,
                         void* ws, void* cuda_stream);
 
+/* Allocation-free forward transform (no counterpart in the paper; a service of
+ * this library).  Same result as su2_forward, but the stage-1 planes go to a
+ * scratch array of SU2_NOALLOC_SCRATCH_BYTES (4 MiB) that this library keeps on
+ * every GPU that loads it, for the whole process lifetime, so callers that
+ * cannot allocate device memory at transform time need no workspace.
+ *  - Plans whose su2_workspace_size exceeds SU2_NOALLOC_SCRATCH_BYTES are
+ *    rejected with SU2_ERR_WORKSPACE (e.g. c64: one function up to N = 64).
+ *  - No cudaMalloc / cudaFree or other allocation happens in this call.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) and caches it; make that first call before any
+ *    stream capture.
+ *  - All calls on a device share the one array and every call rewrites the
+ *    part it reads (nothing needs to start at zero): calls whose kernels
+ *    overlap on the GPU (other streams, or other host threads) race on it;
+ *    serialise them on one stream.
+ *  - grid, coeffs: caller-owned device memory as for su2_forward. */
+#define SU2_NOALLOC_SCRATCH_BYTES (4u << 20)
+su2_status su2_forward_noalloc(su2_plan_t plan, const void* grid, void* coeffs, void* cuda_stream);
+
 /* Synchronises the stream and reports any latched device-side error; clears it. */
 su2_status su2_sync_status(su2_plan_t plan, void* cuda_stream);
 

@@ -201,6 +201,10 @@ su2_status check_exec(su2_plan_t plan, const void* in, const void* out, const vo
 
 }  // namespace
 
+namespace su2 {
+int plan_device(const su2_plan_s* plan) { return plan ? plan->device : -1; }
+}  // namespace su2
+
 extern "C" {
 
 size_t su2_num_coeffs(int N) { return ncoef(N); }

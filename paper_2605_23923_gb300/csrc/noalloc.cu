@@ -1,0 +1,56 @@
+// Allocation-free forward transform: su2_forward with the stage-1 planes held
+// in a fixed-size scratch array that lives in this library's device image
+// instead of a caller-provided workspace.
+//
+// Who needs this: callers that cannot allocate device memory when they run a
+// transform -- code that has no device allocator at hand (a plain C host
+// program that only receives device pointers from elsewhere), code that runs
+// under a fixed memory budget where every cudaMalloc must happen up front, or
+// steady-state loops that must not touch the allocator.  They still create
+// the plan beforehand (su2_plan allocates its small tables once) and pass the
+// grid and coefficient buffers; the planes go to the array below.
+//
+// The array occupies SU2_NOALLOC_SCRATCH_BYTES on every GPU that loads this
+// library, for the lifetime of the process.  Host code cannot use the array's
+// name as a device address, so the device address is looked up once per device
+// with cudaGetSymbolAddress (done by the first call on that device, which
+// should therefore come before any stream capture) and cached.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "../../include/su2fft.h"
+#include "su2_internal.h"
+
+static __device__ __align__(256) unsigned char su2_noalloc_scratch[SU2_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::atomic<void*> g_scratch_ptr[kMaxDevices];
+
+}  // namespace
+
+extern "C" su2_status su2_forward_noalloc(su2_plan_t plan, const void* grid, void* coeffs, void* cuda_stream) {
+    if (!plan || !grid || !coeffs) return SU2_ERR_INVALID_ARG;
+    size_t need = 0;
+    su2_status s = su2_workspace_size(plan, &need);
+    if (s != SU2_OK) return s;
+    if (need > (size_t)SU2_NOALLOC_SCRATCH_BYTES) return SU2_ERR_WORKSPACE;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SU2_ERR_CUDA;
+    const int plan_dev = su2::plan_device(plan);     // su2_forward runs on the plan's device
+    if (plan_dev < 0 || plan_dev >= kMaxDevices) return SU2_ERR_CUDA;
+    void* ptr = g_scratch_ptr[plan_dev].load(std::memory_order_acquire);
+    if (!ptr) {
+        if (plan_dev != dev && cudaSetDevice(plan_dev) != cudaSuccess) return SU2_ERR_CUDA;
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, su2_noalloc_scratch);
+        if (plan_dev != dev) cudaSetDevice(dev);
+        if (e != cudaSuccess || !p) return SU2_ERR_CUDA;
+        g_scratch_ptr[plan_dev].store(p, std::memory_order_release);
+        ptr = p;
+    }
+    return su2_forward(plan, grid, coeffs, ptr, cuda_stream);
+}

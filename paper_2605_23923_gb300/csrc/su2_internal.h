@@ -7,6 +7,8 @@
 
 #include "common.cuh"
 
+struct su2_plan_s;
+
 namespace su2 {
 
 // Stage 1: 2-D DFT over (alpha, gamma) for every beta node (forward), and the
@@ -30,5 +32,8 @@ bool tc_supported(int N);
 // false if the driver entry point is unavailable or the arguments are rejected.
 bool encode_tensor_map_8b(CUtensorMap* map, int rank, const void* base, const cuuint64_t* dims,
                           const cuuint64_t* strides_bytes, const cuuint32_t* box);
+
+// Device ordinal a plan's tables live on.
+int plan_device(const su2_plan_s* plan);
 
 }  // namespace su2
