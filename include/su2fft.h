@@ -106,8 +106,20 @@ typedef struct {
 su2_status su2_plan(su2_plan_t* out, const su2_plan_desc* desc);
 
 /* Bytes of device workspace that su2_forward / su2_inverse / su2_backward
- * need (the stage-1 planes of every function: 2 N^3 complex each). */
+ * need: the stage-1 planes of every function (2 N^3 complex each), followed,
+ * for complex64 bandwidths N = 128, 256, 512, by scratch of the forward 2-D DFT
+ * (a ring of intermediate planes and its counters; tens of MB per bandwidth).
+ * The content is undefined between calls and needs no initialisation. */
 su2_status su2_workspace_size(su2_plan_t plan, size_t* bytes);
+
+/* Element offset of function f's stage-1 planes in the workspace.  Plane
+ * (k, s) of f (beta node k; s = 0: integer l, s = 1: half-integer l) starts at
+ * that offset + (2k + s) N^2 and is stored row-major [mi][ni] (ni fastest):
+ *   F2_s[k][m][n] = w_k/(2N^2) sum_{j1,j2} f[j1,k,j2] e^{i(n alpha_j1 + m gamma_j2)}
+ * with mi = m + N/2, ni = n + N/2 for s = 0 (row and column 0 unused, zero)
+ * and mi = m - 1/2 + N/2, ni = n - 1/2 + N/2 for s = 1 (Sec. 6 first-stage
+ * Proposition; Sec. 4 grid). */
+su2_status su2_plane_offset(su2_plan_t plan, int f, size_t* elems);
 
 /* Element offsets of function f inside the grid and coefficient buffers. */
 su2_status su2_grid_offset(su2_plan_t plan, int f, size_t* elems);

@@ -75,13 +75,15 @@ class Plan:
         _abi.check("su2_grid_elems", self._lib.su2_grid_elems(h, ctypes.byref(ge)))
         _abi.check("su2_coeff_elems", self._lib.su2_coeff_elems(h, ctypes.byref(ce)))
         self.grid_elems, self.coeff_elems = int(ge.value), int(ce.value)
-        self.grid_offsets, self.coeff_offsets = [], []
+        self.grid_offsets, self.coeff_offsets, self.plane_offsets = [], [], []
         for f in range(self.batch):
             o = ctypes.c_size_t()
             _abi.check("su2_grid_offset", self._lib.su2_grid_offset(h, f, ctypes.byref(o)))
             self.grid_offsets.append(int(o.value))
             _abi.check("su2_coeff_offset", self._lib.su2_coeff_offset(h, f, ctypes.byref(o)))
             self.coeff_offsets.append(int(o.value))
+            _abi.check("su2_plane_offset", self._lib.su2_plane_offset(h, f, ctypes.byref(o)))
+            self.plane_offsets.append(int(o.value))
         self._ws = None
 
     # ------------------------------------------------------------------

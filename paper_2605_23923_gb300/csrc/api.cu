@@ -38,6 +38,8 @@ struct Band {
     double2* d_om64 = nullptr;
     float2* d_twist32 = nullptr;
     double2* d_twist64 = nullptr;
+    size_t aux_off = 0;           // stage-1 scratch (two-phase DFT ring) in the workspace
+    int aux_ring = 0;
 };
 
 struct DeviceGuard {
@@ -184,6 +186,8 @@ su2::BandArgs band_args(const su2_plan_s* P, const Band& b) {
     a.ws_group_off = b.fids.empty() ? 0 : P->ws_off[b.fids[0]];
     a.grid_group_off = b.fids.empty() ? 0 : P->grid_off[b.fids[0]];
     a.grid_regular = 1;
+    a.ws_aux_off = b.aux_off;
+    a.aux_ring = b.aux_ring;
     const size_t n3 = (size_t)b.N * b.N * b.N;
     for (size_t i = 0; i < b.fids.size(); ++i)
         if (P->grid_off[b.fids[i]] != a.grid_group_off + i * n3) a.grid_regular = 0;
@@ -276,6 +280,20 @@ su2_status su2_plan(su2_plan_t* out, const su2_plan_desc* desc) {
             P->ws_total += 2 * N * N * N;
         }
     }
+    // scratch of the two-phase stage-1 DFT, after all planes
+    for (auto& kv : P->bands) {
+        if (!su2::fft_forward_two_phase_supported(kv.first, desc->dtype == SU2_C128)) continue;
+        size_t elems = 0;
+        int ring = 0;
+        const cudaError_t ea = su2::fft_forward_aux(kv.first, desc->device, &ring, &elems);
+        if (ea != cudaSuccess) {
+            delete P;
+            return from_cuda(ea);
+        }
+        kv.second.aux_off = P->ws_total;
+        kv.second.aux_ring = ring;
+        P->ws_total += elems;
+    }
     std::vector<double> lf2(2 * Nmax + 2);
     for (size_t k = 0; k < lf2.size(); ++k) lf2[k] = lgamma((double)k + 1.0) / log(2.0);
     cudaError_t e = cudaSuccess;
@@ -316,6 +334,12 @@ su2_status su2_grid_offset(su2_plan_t plan, int f, size_t* elems) {
 su2_status su2_coeff_offset(su2_plan_t plan, int f, size_t* elems) {
     if (!plan || !elems || f < 0 || f >= plan->B) return SU2_ERR_INVALID_ARG;
     *elems = plan->coeff_off[f];
+    return SU2_OK;
+}
+
+su2_status su2_plane_offset(su2_plan_t plan, int f, size_t* elems) {
+    if (!plan || !elems || f < 0 || f >= plan->B) return SU2_ERR_INVALID_ARG;
+    *elems = plan->ws_off[f];
     return SU2_OK;
 }
 

@@ -304,6 +304,9 @@ struct BandArgs {
                                   // the group at ws_group_off + i * 2 N^3)
     size_t grid_group_off;        // grid offset of the group's first function
     int grid_regular;             // 1: function i of the group at grid_group_off + i * N^3
+    size_t ws_aux_off;            // stage-1 scratch of the group (two-phase DFT ring), in
+                                  // complex elements from the workspace start
+    int aux_ring;                 // plane slots of that ring (0: none)
 };
 
 }  // namespace su2

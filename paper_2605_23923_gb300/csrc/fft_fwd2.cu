@@ -1,0 +1,410 @@
+// Stage 1 (Sec. 4 factorised Riemann sum, Sec. 6 first-stage Proposition) for
+// complex64 at N = 128, 256, 512: the 2-D DFT over (alpha, gamma) of every
+// beta-node plane as two phases that meet in L2 instead of in a thread-block
+// cluster.
+//
+//   phase A, item (plane, jb):   16 columns j2 in [16 jb, 16 jb + 16) of the
+//       plane f[., k, .] (one 3-D TMA box, N x 128 B) -> column DFTs over j1,
+//       once plain (sector 0) and once with the pre-twist exp(i pi j1/N)
+//       (sector 1) -> intermediate rows I_s[p][j2] (128-byte segments).
+//   phase B, item (plane, s, pb): the 16 rows p in [16 pb, 16 pb + 16) of I_s
+//       (one 16 N x 8 B bulk copy) -> row DFTs over j2 with the pre-twist
+//       exp(i pi j2/N) for s = 1 -> sign (-1)^{n+m}, weight w_k/(2N^2) ->
+//       planes F2_s[mi][ni] (16 consecutive ni per row: 128-byte segments).
+//
+// The intermediate lives in a ring of plane slots at the end of the workspace;
+// a B item discards the L2 lines it has read (discard.global.L2), so a slot's
+// data normally never reaches DRAM.  Items are numbered in blocks: block t
+// holds the A items of plane t followed by the B items of plane t - D, and item
+// i belongs to CTA i mod G (all CTAs resident).  Ordering is carried by two
+// counters per ring slot: a B item waits until all A items of its plane are
+// done, and an A item reusing a slot waits until the B items of the previous
+// plane in that slot have read it.  Every wait is for an item with a smaller
+// number, so the persistent grid cannot deadlock; every wait is also bounded
+// (it latches the error word and gives up).
+//
+// CTA layout: warps 0 .. CT/32-1 compute, one producer warp issues the loads
+// (after the dependency waits) into a two-slot ring; mbarriers full/empty.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "common.cuh"
+#include "su2_internal.h"
+
+namespace su2 {
+namespace fwd2 {
+
+template <int N>
+struct Cfg {
+    static constexpr int R1 = Radix<N>::R1, R2 = Radix<N>::R2;
+    static constexpr int W = 16;                        // columns per A item, rows per B item
+    static constexpr int NH = N / W;                    // A items per plane; B items per sector
+    static constexpr int NA = NH, NB = 2 * NH, IB = NA + NB;
+    static constexpr int CT = W * (R1 > R2 ? R1 : R2);  // compute threads
+    static constexpr int THREADS = CT + 32;
+    static constexpr int SLOT = W * N;                  // float2 per ring slot
+    static constexpr int NS = 2;                        // ring slots
+    static constexpr int BOXR = N < 256 ? N : 256;      // rows per TMA box (at most 256)
+    static constexpr size_t smem_bytes() {
+        return (size_t)(NS + 1) * SLOT * 8 + (size_t)N * 8 * 2 + (size_t)N * 4 + 4 * 8;
+    }
+    static constexpr int BLOCKS_PER_SM = (N <= 128) ? 4 : (N <= 256 ? 2 : 1);
+};
+
+__device__ __forceinline__ void tma_load_3d_hint(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                                 uint64_t* bar, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint "
+        "[%0], [%1, {%2, %3, %4}], [%5], %6;"
+        ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void mbar_arrive_cta(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+__device__ __forceinline__ void discard_l2_line(const void* p) {
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
+}
+__device__ __forceinline__ void named_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+
+// Spin until *ctr >= target (wrap-safe); bounded like the mbarrier waits.  Once
+// any wait of the launch has timed out (error word set) the others return at
+// once, so a broken dependency costs one timeout, not one per item.
+__device__ __forceinline__ void wait_counter(const unsigned* ctr, unsigned target, int* err) {
+    if ((int)(ld_acquire(ctr) - target) >= 0) return;
+    const long long t0 = clock64();
+    while ((int)(ld_acquire(ctr) - target) < 0) {
+        if (*(volatile int*)err != 0) return;
+        __nanosleep(64);
+        if (clock64() - t0 > 2000000000LL) {
+            atomicExch(err, 1);
+            return;
+        }
+    }
+}
+
+struct Item {
+    bool valid, isA;
+    int plane, jb, s, pb;
+};
+
+template <int N>
+__device__ __forceinline__ Item decode(int i, int nplanes, int D) {
+    using P = Cfg<N>;
+    Item it;
+    const int t = i / P::IB, j = i % P::IB;
+    if (j < P::NA) {
+        it.isA = true;
+        it.plane = t;
+        it.jb = j;
+        it.s = 0;
+        it.pb = 0;
+        it.valid = t < nplanes;
+    } else {
+        it.isA = false;
+        it.plane = t - D;
+        const int jj = j - P::NA;
+        it.s = jj / P::NH;
+        it.pb = jj % P::NH;
+        it.jb = 0;
+        it.valid = it.plane >= 0 && it.plane < nplanes;
+    }
+    return it;
+}
+
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::THREADS, Cfg<N>::BLOCKS_PER_SM)
+fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const float2* __restrict__ grid,
+                  float2* __restrict__ ws, int D, int RING) {
+    using P = Cfg<N>;
+    constexpr int R1 = P::R1, R2 = P::R2, W = P::W, CT = P::CT, SLOT = P::SLOT, NS = P::NS;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float2* S = reinterpret_cast<float2*>(smem_raw);          // [NS][SLOT] ring
+    float2* Y = S + NS * SLOT;                                 // sector-1 columns of an A item
+    float2* om = Y + SLOT;                                     // exp(+2 pi i t/N)
+    float2* tw = om + N;                                       // exp(+i pi t/N)
+    float* wk = reinterpret_cast<float*>(tw + N);
+    uint64_t* full = reinterpret_cast<uint64_t*>(wk + N);      // [NS]
+    uint64_t* empty = full + NS;                               // [NS]
+
+    const int tid = threadIdx.x;
+    const int nplanes = a.nfunc * N;
+    const int nitems = (nplanes + D) * P::IB;
+    float2* ring = ws + a.ws_aux_off;                          // [RING][2][N][N]
+    unsigned* doneA = reinterpret_cast<unsigned*>(ring + (size_t)RING * 2 * N * N);
+    unsigned* doneB = doneA + RING;
+
+    for (int t = tid; t < N; t += blockDim.x) {
+        om[t] = a.om32[t];
+        tw[t] = a.twist32[t];
+        wk[t] = a.w32[t];
+    }
+    if (tid == 0) {
+        for (int b = 0; b < NS; ++b) {
+            mbar_init(&full[b], 1);
+            mbar_init(&empty[b], CT / 32);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    if (tid >= CT) {
+        // ------------------------------------------------------------- producer
+        const int lane = tid - CT;
+        const uint64_t pol = policy_evict_first();
+        int n = 0;
+        for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+            const Item it = decode<N>(i, nplanes, D);
+            if (!it.valid) continue;
+            const int b = n % NS;
+            const unsigned u = (unsigned)(n / NS);
+            ++n;
+            if (u > 0) mbar_wait_bounded(&empty[b], (u - 1) & 1, a.err);
+            const int r = it.plane % RING;
+            const unsigned use = (unsigned)(it.plane / RING);
+            float2* dst = S + b * SLOT;
+            if (it.isA) {
+                const int fb = it.plane / N, k = it.plane % N;
+                if (lane == 0 && use > 0) wait_counter(&doneB[r], use * P::NB, a.err);
+                if (a.grid_regular) {
+                    if (lane == 0) {
+                        mbar_arrive_expect_tx(&full[b], (uint32_t)(SLOT * 8));
+#pragma unroll
+                        for (int h = 0; h < N / P::BOXR; ++h)
+                            tma_load_3d_hint(dst + h * P::BOXR * W, &gmap, it.jb * W, k, fb * N + h * P::BOXR,
+                                             &full[b], pol);
+                    }
+                } else {
+                    const float2* src = grid + a.grid_off[a.fidx[fb]] + (size_t)k * N + it.jb * W;
+                    if (lane == 0) mbar_arrive_expect_tx(&full[b], (uint32_t)(SLOT * 8));
+                    __syncwarp();
+                    for (int j1 = lane; j1 < N; j1 += 32)
+                        bulk_g2s(dst + j1 * W, src + (size_t)j1 * N * N, (uint32_t)(W * 8), &full[b]);
+                }
+            } else if (lane == 0) {
+                wait_counter(&doneA[r], (use + 1) * P::NA, a.err);
+                fence_proxy_async_global();
+                const float2* src = ring + ((size_t)(r * 2 + it.s) * N + it.pb * W) * N;
+                mbar_arrive_expect_tx(&full[b], (uint32_t)(SLOT * 8));
+                bulk_g2s(dst, src, (uint32_t)(SLOT * 8), &full[b]);
+            }
+            __syncwarp();
+        }
+        return;
+    }
+
+    // ----------------------------------------------------------------- compute
+    const int warp = tid >> 5, lane = tid & 31;
+    int n = 0;
+    for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+        const Item it = decode<N>(i, nplanes, D);
+        if (!it.valid) continue;
+        const int b = n % NS;
+        const unsigned u = (unsigned)(n / NS);
+        ++n;
+        float2* X = S + b * SLOT;
+        const int r = it.plane % RING;
+        const int fb = it.plane / N, k = it.plane % N;
+        mbar_wait_bounded(&full[b], u & 1, a.err);
+
+        if (it.isA) {
+            // Pass a: R2-point DFTs over j1 = ia + R1*b (stride R1), both sectors.
+            if (tid < W * R1) {
+                const int jc = tid % W, ia = tid / W;
+                float2 v[R2], w[R2];
+#pragma unroll
+                for (int q = 0; q < R2; ++q) {
+                    v[q] = X[(ia + R1 * q) * W + jc];
+                    w[q] = cmul(v[q], tw[ia + R1 * q]);
+                }
+                dft_reg<R2, 1, float>(w);
+#pragma unroll
+                for (int q = 0; q < R2; ++q) Y[(ia + R1 * q) * W + jc] = (q == 0) ? w[0] : cmul(w[q], om[ia * q]);
+                dft_reg<R2, 1, float>(v);
+                named_sync(1, CT);
+#pragma unroll
+                for (int q = 0; q < R2; ++q) X[(ia + R1 * q) * W + jc] = (q == 0) ? v[0] : cmul(v[q], om[ia * q]);
+            } else {
+                named_sync(1, CT);
+            }
+            named_sync(1, CT);
+            // Pass b: R1-point DFTs over ia; bin p = qb + R2*qa -> intermediate row p.
+            if (tid < W * R2) {
+                const int jc = tid % W, qb = tid / W;
+                float2* I0 = ring + (size_t)(r * 2) * N * N + it.jb * W + jc;
+                float2* I1 = I0 + (size_t)N * N;
+                float2 v[R1];
+#pragma unroll
+                for (int ia = 0; ia < R1; ++ia) v[ia] = X[(ia + R1 * qb) * W + jc];
+                dft_reg<R1, 1, float>(v);
+#pragma unroll
+                for (int qa = 0; qa < R1; ++qa) I0[(size_t)(qb + R2 * qa) * N] = v[qa];
+#pragma unroll
+                for (int ia = 0; ia < R1; ++ia) v[ia] = Y[(ia + R1 * qb) * W + jc];
+                dft_reg<R1, 1, float>(v);
+#pragma unroll
+                for (int qa = 0; qa < R1; ++qa) I1[(size_t)(qb + R2 * qa) * N] = v[qa];
+            }
+            named_sync(1, CT);                   // slot and Y read; intermediate written
+            if (lane == 0) mbar_arrive_cta(&empty[b]);
+            if (tid == 0) {
+                __threadfence();
+                atomicAdd(&doneA[r], 1u);
+            }
+        } else {
+            // The rows are in shared memory: drop them from L2 and release the slot.
+            {
+                const char* src = reinterpret_cast<const char*>(ring + ((size_t)(r * 2 + it.s) * N + it.pb * W) * N);
+                for (int l = tid; l < SLOT * 8 / 128; l += CT) discard_l2_line(src + (size_t)l * 128);
+            }
+            named_sync(1, CT);
+            if (tid == 0) {
+                __threadfence();
+                atomicAdd(&doneB[r], 1u);
+            }
+            // Pass a: R2-point DFTs over j2 = ia + R1*q, rows pl; written back XOR-swizzled.
+            if (tid < W * R1) {
+                const int ia = tid % R1, pl = tid / R1;
+                float2 v[R2];
+#pragma unroll
+                for (int q = 0; q < R2; ++q) {
+                    v[q] = X[pl * N + ia + R1 * q];
+                    if (it.s) v[q] = cmul(v[q], tw[ia + R1 * q]);
+                }
+                dft_reg<R2, 1, float>(v);
+#pragma unroll
+                for (int q = 1; q < R2; ++q) v[q] = cmul(v[q], om[ia * q]);
+                named_sync(1, CT);
+#pragma unroll
+                for (int q = 0; q < R2; ++q) X[pl * N + ((ia + R1 * q) ^ (pl & 15))] = v[q];
+            } else {
+                named_sync(1, CT);
+            }
+            named_sync(1, CT);
+            // Pass b: R1-point DFTs; output bin q = qb + R2*qa; 16 consecutive ni per row.
+            if (tid < W * R2) {
+                const int pl = tid % W, qb = tid / W;
+                float2 v[R1];
+#pragma unroll
+                for (int ia = 0; ia < R1; ++ia) v[ia] = X[pl * N + ((ia + R1 * qb) ^ (pl & 15))];
+                named_sync(2, W * R2);
+                if (lane == 0) mbar_arrive_cta(&empty[b]);
+                dft_reg<R1, 1, float>(v);
+                const float scale = wk[k] / (2.f * (float)N * (float)N);
+                const size_t plane_off = a.grid_regular ? a.ws_group_off + (size_t)fb * 2 * N * N * N
+                                                        : a.ws_off[a.fidx[fb]];
+                float2* out = ws + plane_off + ((size_t)k * 2 + it.s) * N * N;
+                const int p = it.pb * W + pl;
+                const int ni = (p + N / 2) & (N - 1);
+                float sc = ((ni + qb) & 1) ? -scale : scale;     // parity of mi = parity of qb
+                if (it.s) sc = -sc;
+                const bool zero_col = (it.s == 0 && ni == 0);
+#pragma unroll
+                for (int qa = 0; qa < R1; ++qa) {
+                    const int q = qb + R2 * qa;
+                    const int mi = (q + N / 2) & (N - 1);
+                    float2 val = make_float2(v[qa].x * sc, v[qa].y * sc);
+                    if (zero_col || (it.s == 0 && mi == 0)) val = make_float2(0.f, 0.f);
+                    __stcs(out + (size_t)mi * N + ni, val);
+                }
+            } else if (lane == 0 && (warp * 32) >= W * R2) {
+                mbar_arrive_cta(&empty[b]);
+            }
+        }
+    }
+}
+
+// Work-distribution parameters shared by the plan (workspace size) and the launch.
+template <int N>
+static cudaError_t geometry(int device, int* G, int* D, int* RING) {
+    using P = Cfg<N>;
+    int sms = 0, per = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) return e;
+    auto kern = fft_fwd_two_phase<N>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::smem_bytes());
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, P::THREADS, P::smem_bytes());
+    if (e != cudaSuccess) return e;
+    if (per < 1) return cudaErrorInvalidConfiguration;
+    *G = sms * per;
+    const int inflight = (2 * *G + P::IB - 1) / P::IB;        // planes touched by two items per CTA
+    *D = 2 * inflight + 2;
+    *RING = *D + inflight + 4;
+    return cudaSuccess;
+}
+
+template <int N>
+static cudaError_t launch_n(const BandArgs& a, const void* in, void* out, cudaStream_t st) {
+    using P = Cfg<N>;
+    int dev = 0, G = 0, D = 0, RING = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = geometry<N>(dev, &G, &D, &RING)) != cudaSuccess) return e;
+    if (RING != a.aux_ring) return cudaErrorInvalidValue;          // plan built for another device shape
+    float2* ring = (float2*)out + a.ws_aux_off;
+    unsigned* ctr = reinterpret_cast<unsigned*>(ring + (size_t)RING * 2 * N * N);
+    if ((e = cudaMemsetAsync(ctr, 0, sizeof(unsigned) * 2 * RING, st)) != cudaSuccess) return e;
+    CUtensorMap gmap;
+    memset(&gmap, 0, sizeof(gmap));
+    BandArgs b = a;
+    if (b.grid_regular) {
+        const cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)a.nfunc * N};
+        const cuuint64_t strides[2] = {(cuuint64_t)N * 8, (cuuint64_t)N * N * 8};
+        const cuuint32_t box[3] = {(cuuint32_t)P::W, 1, (cuuint32_t)P::BOXR};
+        const void* base = (const float2*)in + a.grid_group_off;
+        if (!encode_tensor_map_8b(&gmap, 3, base, dims, strides, box)) b.grid_regular = 0;
+    }
+    const int nitems = (a.nfunc * N + D) * P::IB;
+    const int grid = G < nitems ? G : nitems;
+    fft_fwd_two_phase<N><<<grid, P::THREADS, P::smem_bytes(), st>>>(b, gmap, (const float2*)in, (float2*)out, D,
+                                                                   RING);
+    return cudaGetLastError();
+}
+
+}  // namespace fwd2
+
+bool fft_forward_two_phase_supported(int N, bool fp64) { return !fp64 && (N == 128 || N == 256 || N == 512); }
+
+cudaError_t fft_forward_aux(int N, int device, int* ring, size_t* elems) {
+    int G = 0, D = 0, R = 0;
+    cudaError_t e;
+    switch (N) {
+        case 128: e = fwd2::geometry<128>(device, &G, &D, &R); break;
+        case 256: e = fwd2::geometry<256>(device, &G, &D, &R); break;
+        case 512: e = fwd2::geometry<512>(device, &G, &D, &R); break;
+        default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    *ring = R;
+    // ring planes (2 N^2 complex each) + 2 R counters, rounded up to 16 bytes
+    *elems = (size_t)R * 2 * N * N + ((size_t)2 * R * sizeof(unsigned) + 15) / 16 * 2;
+    return cudaSuccess;
+}
+
+cudaError_t launch_fft_forward_two_phase(const BandArgs& a, const void* grid, void* ws, cudaStream_t st) {
+    if (a.nfunc <= 0) return cudaSuccess;
+    switch (a.N) {
+        case 128: return fwd2::launch_n<128>(a, grid, ws, st);
+        case 256: return fwd2::launch_n<256>(a, grid, ws, st);
+        case 512: return fwd2::launch_n<512>(a, grid, ws, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace su2

@@ -1,0 +1,99 @@
+"""Stage 1 alone (su2_forward_stage1) against the oracle's torus double sum.
+
+The planes F2_s[k][m][n] = w_k/(2N^2) sum f e^{i(n alpha + m gamma)} are
+compared element by element on sampled beta nodes (both sectors, every (m, n);
+the unused Nyquist row and column of sector 0 must be zero), at the bandwidths
+that run the two-phase complex64 kernel (N = 128, 256, 512) and on a ragged
+batch whose bandwidth groups are not regularly strided in the grid buffer.
+"""
+import numpy as np
+import pytest
+
+import su2inputs as I
+from oracle import grid as OG
+from oracle import quadrature as OQ
+from oracle import transform as T
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def su2():
+    import paper_2605_23923_gb300 as m
+    from paper_2605_23923_gb300 import build
+    build.build()
+    return m
+
+
+def expected_planes(f, k):
+    """Both sectors of plane k in the workspace layout [mi][ni], from the oracle."""
+    N = f.shape[0]
+    al, ga = OG.alpha_nodes(N), OG.gamma_nodes(N)
+    w = OQ.weights(N, "cc")
+    out = []
+    for sector in ("int", "half"):
+        idx = T.sector_indices(N, sector)
+        F = T.torus_dft(f[:, k:k + 1, :], idx, idx, al, ga)[0]          # [n, m]
+        plane = np.zeros((N, N), dtype=np.complex128)
+        pos = (idx + (0 if sector == "int" else -1)) // 2 + N // 2        # mi / ni of doubled index
+        plane[np.ix_(pos, pos)] = (F.T) * w[k] / (2.0 * N * N)            # rows m, columns n
+        out.append(plane)
+    return out
+
+
+def check_planes(plan, ws, f, fi, ks):
+    N = f.shape[0]
+    c = ws.view(torch.complex64)
+    base = plan.plane_offsets[fi]
+    worst = scale = 0.0
+    for k in ks:
+        for s, ref in enumerate(expected_planes(f, k)):
+            o = base + (2 * k + s) * N * N
+            got = c[o:o + N * N].cpu().numpy().astype(np.complex128).reshape(N, N)
+            worst = max(worst, float(np.max(np.abs(got - ref))))
+            scale = max(scale, float(np.max(np.abs(ref))))
+            if s == 0:
+                assert np.all(got[0, :] == 0) and np.all(got[:, 0] == 0)
+    assert worst / scale < TOL, (fi, worst / scale)
+
+
+@pytest.mark.parametrize("N,B", [(64, 2), (128, 3), (256, 2), (512, 1)])
+def test_stage1_planes_uniform(su2, N, B):
+    rng = np.random.default_rng(40 + N)
+    grids = [I.draw_grid_gaussian((N, N, N), rng).astype(np.complex64) for _ in range(B)]
+    plan = su2.Plan(N=N, batch=B, dtype="c64")
+    x = torch.from_numpy(np.concatenate([g.reshape(-1) for g in grids])).cuda()
+    ws = plan.forward_stage1(x)
+    plan.sync_status()
+    ks = [0, 1, N // 2 - 1, N // 2, N - 2, N - 1] + list(rng.integers(0, N, 3))
+    for fi, g in enumerate(grids):
+        check_planes(plan, ws, g.astype(np.complex128), fi, ks)
+
+
+def test_stage1_planes_ragged(su2):
+    Ns = [128, 64, 128, 256, 128]
+    rng = np.random.default_rng(47)
+    grids = [I.draw_grid_gaussian((n, n, n), rng).astype(np.complex64) for n in Ns]
+    plan = su2.Plan(Ns=Ns, dtype="c64")
+    x = torch.from_numpy(np.concatenate([g.reshape(-1) for g in grids])).cuda()
+    ws = plan.forward_stage1(x)
+    plan.sync_status()
+    for fi, (n, g) in enumerate(zip(Ns, grids)):
+        check_planes(plan, ws, g.astype(np.complex128), fi, [0, 5, n // 2, n - 1])
+
+
+def test_stage1_repeat_reuses_scratch(su2):
+    """Back-to-back launches on one workspace (the counters are reset per launch)."""
+    N, B = 256, 2
+    rng = np.random.default_rng(48)
+    plan = su2.Plan(N=N, batch=B, dtype="c64")
+    for rep in range(3):
+        grids = [I.draw_grid_gaussian((N, N, N), rng).astype(np.complex64) for _ in range(B)]
+        x = torch.from_numpy(np.concatenate([g.reshape(-1) for g in grids])).cuda()
+        ws = plan.forward_stage1(x)
+        plan.sync_status()
+        for fi, g in enumerate(grids):
+            check_planes(plan, ws, g.astype(np.complex128), fi, [3, N - 4])
