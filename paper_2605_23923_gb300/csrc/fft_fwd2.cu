@@ -50,7 +50,7 @@ struct Cfg {
     static constexpr size_t smem_bytes() {
         return (size_t)(NS + 1) * SLOT * 8 + (size_t)N * 8 * 2 + (size_t)N * 4 + 4 * 8;
     }
-    static constexpr int BLOCKS_PER_SM = (N <= 128) ? 4 : (N <= 256 ? 2 : 1);
+    static constexpr int BLOCKS_PER_SM = (N <= 128) ? 3 : (N <= 256 ? 2 : 1);
 };
 
 __device__ __forceinline__ void tma_load_3d_hint(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
@@ -130,7 +130,7 @@ __device__ __forceinline__ Item decode(int i, int nplanes, int D) {
 template <int N>
 __global__ void __launch_bounds__(Cfg<N>::THREADS, Cfg<N>::BLOCKS_PER_SM)
 fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const float2* __restrict__ grid,
-                  float2* __restrict__ ws, int D, int RING) {
+                  float2* __restrict__ ws, int D, int RING, int discard_ok) {
     using P = Cfg<N>;
     constexpr int R1 = P::R1, R2 = P::R2, W = P::W, CT = P::CT, SLOT = P::SLOT, NS = P::NS;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -197,11 +197,10 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
                         bulk_g2s(dst + j1 * W, src + (size_t)j1 * N * N, (uint32_t)(W * 8), &full[b]);
                 }
             } else if (lane == 0) {
+                // B item: the compute threads read the rows from L2 themselves; the
+                // slot only serves as their transpose buffer.  Signal the dependency.
                 wait_counter(&doneA[r], (use + 1) * P::NA, a.err);
-                fence_proxy_async_global();
-                const float2* src = ring + ((size_t)(r * 2 + it.s) * N + it.pb * W) * N;
-                mbar_arrive_expect_tx(&full[b], (uint32_t)(SLOT * 8));
-                bulk_g2s(dst, src, (uint32_t)(SLOT * 8), &full[b]);
+                mbar_arrive_cta(&full[b]);
             }
             __syncwarp();
         }
@@ -239,6 +238,7 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
                 named_sync(1, CT);
 #pragma unroll
                 for (int q = 0; q < R2; ++q) X[(ia + R1 * q) * W + jc] = (q == 0) ? v[0] : cmul(v[q], om[ia * q]);
+                fence_proxy_async_smem();   // before the slot is refilled by TMA
             } else {
                 named_sync(1, CT);
             }
@@ -267,9 +267,29 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
                 atomicAdd(&doneA[r], 1u);
             }
         } else {
-            // The rows are in shared memory: drop them from L2 and release the slot.
+            // Pass a: R2-point DFTs over j2 = ia + R1*q of row pl, read straight from
+            // the intermediate in L2; written back XOR-swizzled into the slot.
+            const float2* rows = ring + ((size_t)(r * 2 + it.s) * N + it.pb * W) * N;
             {
-                const char* src = reinterpret_cast<const char*>(ring + ((size_t)(r * 2 + it.s) * N + it.pb * W) * N);
+                const int ia = tid % R1, pl = tid / R1;            // W * R1 == CT
+                float2 v[R2];
+#pragma unroll
+                for (int q = 0; q < R2; ++q) v[q] = __ldcs(rows + pl * N + ia + R1 * q);
+                if (it.s) {
+#pragma unroll
+                    for (int q = 0; q < R2; ++q) v[q] = cmul(v[q], tw[ia + R1 * q]);
+                }
+                dft_reg<R2, 1, float>(v);
+#pragma unroll
+                for (int q = 1; q < R2; ++q) v[q] = cmul(v[q], om[ia * q]);
+                named_sync(1, CT);        // every load of the item has been consumed
+#pragma unroll
+                for (int q = 0; q < R2; ++q) X[pl * N + ((ia + R1 * q) ^ (pl & 15))] = v[q];
+                fence_proxy_async_smem();   // before the slot is refilled by TMA
+            }
+            // The rows are in registers / shared memory: drop them from L2, release them.
+            if (discard_ok) {             // ring rows on 128-byte lines: no line is shared
+                const char* src = reinterpret_cast<const char*>(rows);
                 for (int l = tid; l < SLOT * 8 / 128; l += CT) discard_l2_line(src + (size_t)l * 128);
             }
             named_sync(1, CT);
@@ -277,25 +297,6 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
                 __threadfence();
                 atomicAdd(&doneB[r], 1u);
             }
-            // Pass a: R2-point DFTs over j2 = ia + R1*q, rows pl; written back XOR-swizzled.
-            if (tid < W * R1) {
-                const int ia = tid % R1, pl = tid / R1;
-                float2 v[R2];
-#pragma unroll
-                for (int q = 0; q < R2; ++q) {
-                    v[q] = X[pl * N + ia + R1 * q];
-                    if (it.s) v[q] = cmul(v[q], tw[ia + R1 * q]);
-                }
-                dft_reg<R2, 1, float>(v);
-#pragma unroll
-                for (int q = 1; q < R2; ++q) v[q] = cmul(v[q], om[ia * q]);
-                named_sync(1, CT);
-#pragma unroll
-                for (int q = 0; q < R2; ++q) X[pl * N + ((ia + R1 * q) ^ (pl & 15))] = v[q];
-            } else {
-                named_sync(1, CT);
-            }
-            named_sync(1, CT);
             // Pass b: R1-point DFTs; output bin q = qb + R2*qa; 16 consecutive ni per row.
             if (tid < W * R2) {
                 const int pl = tid % W, qb = tid / W;
@@ -372,8 +373,9 @@ static cudaError_t launch_n(const BandArgs& a, const void* in, void* out, cudaSt
     }
     const int nitems = (a.nfunc * N + D) * P::IB;
     const int grid = G < nitems ? G : nitems;
+    const int discard_ok = ((uintptr_t)ring % 128) == 0;
     fft_fwd_two_phase<N><<<grid, P::THREADS, P::smem_bytes(), st>>>(b, gmap, (const float2*)in, (float2*)out, D,
-                                                                   RING);
+                                                                   RING, discard_ok);
     return cudaGetLastError();
 }
 
@@ -392,8 +394,9 @@ cudaError_t fft_forward_aux(int N, int device, int* ring, size_t* elems) {
     }
     if (e != cudaSuccess) return e;
     *ring = R;
-    // ring planes (2 N^2 complex each) + 2 R counters, rounded up to 16 bytes
-    *elems = (size_t)R * 2 * N * N + ((size_t)2 * R * sizeof(unsigned) + 15) / 16 * 2;
+    // ring planes (2 N^2 complex each) + 2 R counters, rounded up to 256 bytes so
+    // that the next bandwidth's ring starts on a 128-byte L2 line as well
+    *elems = (size_t)R * 2 * N * N + ((size_t)2 * R * sizeof(unsigned) + 255) / 256 * 32;
     return cudaSuccess;
 }
 

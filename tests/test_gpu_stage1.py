@@ -97,3 +97,21 @@ def test_stage1_repeat_reuses_scratch(su2):
         plan.sync_status()
         for fi, g in enumerate(grids):
             check_planes(plan, ws, g.astype(np.complex128), fi, [3, N - 4])
+
+
+def test_stage1_workspace_only_16_byte_aligned(su2):
+    """A workspace that is 16-byte but not 128-byte aligned (allowed by the C ABI):
+    the intermediate ring then shares L2 lines with its neighbours and must not be
+    discarded; the planes stay exact."""
+    N, B = 256, 2
+    rng = np.random.default_rng(49)
+    grids = [I.draw_grid_gaussian((N, N, N), rng).astype(np.complex64) for _ in range(B)]
+    plan = su2.Plan(N=N, batch=B, dtype="c64")
+    raw = torch.empty(plan.workspace_bytes + 256, dtype=torch.uint8, device="cuda")
+    ws = raw[16:16 + plan.workspace_bytes]
+    assert ws.data_ptr() % 128 == 16
+    x = torch.from_numpy(np.concatenate([g.reshape(-1) for g in grids])).cuda()
+    plan.forward_stage1(x, ws=ws)
+    plan.sync_status()
+    for fi, g in enumerate(grids):
+        check_planes(plan, ws, g.astype(np.complex128), fi, [0, 7, N // 2, N - 1])
