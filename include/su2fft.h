@@ -118,7 +118,10 @@ su2_status su2_workspace_size(su2_plan_t plan, size_t* bytes);
  *   F2_s[k][m][n] = w_k/(2N^2) sum_{j1,j2} f[j1,k,j2] e^{i(n alpha_j1 + m gamma_j2)}
  * with mi = m + N/2, ni = n + N/2 for s = 0 (row and column 0 unused, zero)
  * and mi = m - 1/2 + N/2, ni = n - 1/2 + N/2 for s = 1 (Sec. 6 first-stage
- * Proposition; Sec. 4 grid). */
+ * Proposition; Sec. 4 grid).  Plans of algorithm SU2_ALGO_TC_BF16X3 store the
+ * same values tile-major instead: element (k, s, mi, ni) at that offset +
+ * s N^3 + mi N^2 + (ni / 4) 4N + 4k + ni % 4 (four consecutive n of all beta
+ * nodes contiguous, the operand tiles of the tensor-core contraction). */
 su2_status su2_plane_offset(su2_plan_t plan, int f, size_t* elems);
 
 /* Element offsets of function f inside the grid and coefficient buffers. */

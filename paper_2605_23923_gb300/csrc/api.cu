@@ -15,6 +15,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <map>
 #include <new>
 #include <vector>
@@ -31,6 +32,7 @@ struct Band {
     double* d_cosb = nullptr;
     double* d_log2c = nullptr;
     double* d_log2s = nullptr;
+    float4* d_seed32 = nullptr;
     double* d_w64 = nullptr;
     float* d_w32 = nullptr;
     float2* d_xsplit = nullptr;
@@ -153,6 +155,23 @@ cudaError_t build_band(su2_plan_s* P, Band& b) {
     if ((e = P->upload(&b.d_cosb, cosb.data(), N)) != cudaSuccess) return e;
     if ((e = P->upload(&b.d_log2c, l2c.data(), N)) != cudaSuccess) return e;
     if ((e = P->upload(&b.d_log2s, l2s.data(), N)) != cudaSuccess) return e;
+    {
+        // split logarithms for the FP32 seed evaluation (exact products with pc, ps < 256)
+        std::vector<float4> s32(N);
+        auto split = [](double v, float* hi, float* lo) {
+            if (!std::isfinite(v)) { *hi = 0.f; *lo = 0.f; return; }   // pole: the seed is 0 there
+            const double h = std::rint(v * 2048.0) / 2048.0;
+            *hi = (float)h;
+            *lo = (float)(v - h);
+        };
+        for (int k = 0; k < N; ++k) {
+            float ch, cl, sh, sl;
+            split(l2c[k], &ch, &cl);
+            split(l2s[k], &sh, &sl);
+            s32[k] = make_float4(ch, cl, sh, sl);
+        }
+        if ((e = P->upload(&b.d_seed32, s32.data(), N)) != cudaSuccess) return e;
+    }
     if ((e = P->upload(&b.d_w64, w.data(), N)) != cudaSuccess) return e;
     if ((e = P->upload(&b.d_w32, w32.data(), N)) != cudaSuccess) return e;
     if ((e = P->upload(&b.d_xsplit, xs.data(), N)) != cudaSuccess) return e;
@@ -174,6 +193,7 @@ su2::BandArgs band_args(const su2_plan_s* P, const Band& b) {
     a.cosb = b.d_cosb;
     a.log2c = b.d_log2c;
     a.log2s = b.d_log2s;
+    a.seed32 = b.d_seed32;
     a.w64 = b.d_w64;
     a.w32 = b.d_w32;
     a.xsplit = b.d_xsplit;
@@ -188,6 +208,7 @@ su2::BandArgs band_args(const su2_plan_s* P, const Band& b) {
     a.grid_regular = 1;
     a.ws_aux_off = b.aux_off;
     a.aux_ring = b.aux_ring;
+    a.ws_tile_major = (P->algo == SU2_ALGO_TC_BF16X3) ? 1 : 0;
     const size_t n3 = (size_t)b.N * b.N * b.N;
     for (size_t i = 0; i < b.fids.size(); ++i)
         if (P->grid_off[b.fids[i]] != a.grid_group_off + i * n3) a.grid_regular = 0;
@@ -282,7 +303,9 @@ su2_status su2_plan(su2_plan_t* out, const su2_plan_desc* desc) {
     }
     // scratch of the two-phase stage-1 DFT, after all planes
     for (auto& kv : P->bands) {
+        // complex64 at N >= 128; the tensor-core path also at N = 64 (its planes are tile-major)
         if (!su2::fft_forward_two_phase_supported(kv.first, desc->dtype == SU2_C128)) continue;
+        if (kv.first < 128 && algo != SU2_ALGO_TC_BF16X3) continue;
         size_t elems = 0;
         int ring = 0;
         const cudaError_t ea = su2::fft_forward_aux(kv.first, desc->device, &ring, &elems);

@@ -290,6 +290,9 @@ struct BandArgs {
     const double* cosb;           // cos(beta_k)
     const double* log2c;          // log2 cos(beta_k/2)
     const double* log2s;          // log2 sin(beta_k/2)
+    const float4* seed32;         // (c_hi, c_lo, s_hi, s_lo): log2 cos(beta_k/2) = c_hi + c_lo,
+                                  // log2 sin(beta_k/2) = s_hi + s_lo, hi parts on a 2^-11 grid
+                                  // (so pc * hi is exact in FP32 for pc < 2^8); 0 at the poles
     const double* w64;            // beta weights w_k
     const float* w32;
     const float2* xsplit;         // (hi, lo) float split of cos(beta_k)
@@ -307,6 +310,8 @@ struct BandArgs {
     size_t ws_aux_off;            // stage-1 scratch of the group (two-phase DFT ring), in
                                   // complex elements from the workspace start
     int aux_ring;                 // plane slots of that ring (0: none)
+    int ws_tile_major;            // 1: stage-1 planes of a function stored [s][mi][ni/4][k][ni%4]
+                                  // (tensor-core plans), 0: [k][s][mi][ni]
 };
 
 }  // namespace su2

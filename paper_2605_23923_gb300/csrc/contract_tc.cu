@@ -14,6 +14,7 @@
 // One persistent CTA per SM owns tiles of 4 consecutive n at fixed
 // (sector, m) and 64 functions.  Warp roles, connected by mbarriers:
 //   warp 0      TMA: F2 chunk [64 functions][16 nodes][4 n] into a staging ring
+//               (the planes are tile-major, so a function's chunk is 512 B)
 //   warp 1      MMA issue (one thread), tensor-memory owner
 //   warps 2-5, 10-11  convert staged F2 (fp32) to the BF16 hi/lo A operands
 //   warps 6-9   two generator groups (even / odd chunks): the d-values of the
@@ -58,7 +59,9 @@ constexpr int OFF_A = OFF_STG + 2 * STAGE_BYTES;
 constexpr int OFF_B = OFF_A + ((2 * A_BYTES + 127) / 128) * 128;
 constexpr int OFF_COEF = OFF_B + 2 * B_BYTES;
 constexpr int OFF_TAB = OFF_COEF + 2 * NP * RMAX * (int)sizeof(StepCoef<float>);
-constexpr int TAB_BYTES = NMAX * 8 * 3 + NMAX * 8;   // log2c, log2s, lf2 (double) + xsplit (float2)
+// seed32 (float4) + lf2 (double) + xsplit (float2) + seed parameters of the pairs
+struct GenPair { float Khi, Klo, pc, ps, sg; int zero_c, zero_s, pad; };
+constexpr int TAB_BYTES = NMAX * 16 + NMAX * 8 + NMAX * 8 + 2 * NP * (int)sizeof(GenPair);
 constexpr int OFF_BAR = OFF_TAB + TAB_BYTES;
 constexpr int NBAR = 12;
 constexpr int SMEM_BYTES = OFF_BAR + NBAR * 8 + 16;
@@ -148,15 +151,14 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
     uint64_t* bar_accfull = bars + 10; //     accumulators of a tile final (tcgen05.commit)
     uint64_t* bar_accfree = bars + 11; //     epilogue drained TMEM        (count 4)
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + NBAR);
-    double* t_l2c = reinterpret_cast<double*>(smem + OFF_TAB);
-    double* t_l2s = t_l2c + NMAX;
-    double* t_lf2 = t_l2s + NMAX;
+    float4* t_seed = reinterpret_cast<float4*>(smem + OFF_TAB);
+    double* t_lf2 = reinterpret_cast<double*>(t_seed + NMAX);
     float2* t_xs = reinterpret_cast<float2*>(t_lf2 + NMAX);
+    GenPair* t_gp = reinterpret_cast<GenPair*>(t_xs + NMAX);      // [2 groups][NP]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     for (int t = tid; t < N; t += THREADS) {
-        t_l2c[t] = a.log2c[t];
-        t_l2s[t] = a.log2s[t];
+        t_seed[t] = a.seed32[t];
         t_lf2[t] = a.lf2[t];
         t_xs[t] = a.xsplit[t];
     }
@@ -182,12 +184,6 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
     tc_fence_after();
     const uint32_t taddr = *tslot;
 
-    // seed tables in shared memory (generic pointers into this CTA's smem)
-    BandArgs as = a;
-    as.log2c = t_l2c;
-    as.log2s = t_l2s;
-    as.lf2 = t_lf2;
-    as.xsplit = t_xs;
 
     const int ntiles = 2 * N * (N / NP);
     const int nbb = (a.nfunc + BM - 1) / BM;
@@ -207,7 +203,7 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
                     const uint32_t u = g >> 1;
                     if (u > 0) mbar_wait_bounded(&bar_sfree[st], (u - 1) & 1, a.err);
                     mbar_arrive_expect_tx(&bar_full[st], (uint32_t)STAGE_BYTES);
-                    tma_load_5d(smem + OFF_STG + st * STAGE_BYTES, &tmap, tl.nb * NP, tl.mi, tl.s, c * KC, bb * BM,
+                    tma_load_5d(smem + OFF_STG + st * STAGE_BYTES, &tmap, c * KC * NP, tl.nb, tl.mi, tl.s, bb * BM,
                                 &bar_full[st]);
                 }
             }
@@ -290,61 +286,122 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
         }
     } else if (warp >= W_GEN && warp < W_GEN + 4) {
         // ------------------------------------------------------------------ recurrence -> B (bf16 hi/lo)
+        // Thread (p, kk) runs the chain of pair p at node c*KC + kk for the chunks of
+        // its group's stage.  Seeds in FP32 from the split logarithms (exact
+        // products and sums; only the pair's factorial ratio K is FP64, once per
+        // tile).  Range extension: value = cur * 2^(-120 E); while E > 0 the value is
+        // below 2^-39 and enters as 0.  A warp whose chains all have E = 0 runs the
+        // plain recurrence; otherwise cur is renormalised once per 8 rows when
+        // |cur| >= 2^40 (8 steps grow it by less than 2^41, so it stays finite).
         const int grp = (warp - W_GEN) >> 1;               // handles the chunks of stage grp
         const int gt = tid - W_GEN * 32 - grp * 64;        // 0..63
         const int p = gt >> 4, kk = gt & 15;
         StepCoef<float>* coef = reinterpret_cast<StepCoef<float>*>(smem + OFF_COEF) + grp * NP * RMAX;
+        GenPair* gp = t_gp + grp * NP;
         uint32_t g = 0;
         for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
             Tile<NP> tl;
             tl.decode(N, item / nbb);
             if (!tl.any) continue;
             const int Lt = tl.L, nmma = (Lt + 15) & ~15;
-            named_sync(1 + grp, 64);                       // previous tile's coefficients no longer read
+            named_sync(1 + grp, 64);                       // previous tile's tables no longer read
             for (int idx = gt; idx < NP * (Lt - 1); idx += 64) {
                 const int pp = idx % NP, r = idx / NP;
                 const int J = tl.j0 + 2 * r;
                 if (J >= tl.mu2[pp]) coef[pp * RMAX + r] = step_coef<float>(J, tl.n2[pp], tl.m2);
             }
+            if (gt < NP) {
+                const SeedParams sp = seed_params(t_lf2, tl.n2[gt], tl.m2);
+                const double kh = rint(sp.K * 2048.0) / 2048.0;
+                GenPair q;
+                q.Khi = (float)kh;
+                q.Klo = (float)(sp.K - kh);
+                q.pc = (float)sp.pc;
+                q.ps = (float)sp.ps;
+                q.sg = (float)sp.sg;
+                q.zero_c = sp.pc > 0;
+                q.zero_s = sp.ps > 0;
+                gp[gt] = q;
+            }
             named_sync(1 + grp, 64);
+            const bool valid = tl.valid[p];
+            const int rp = valid ? (tl.mu2[p] - tl.j0) / 2 : nmma;   // first row of my pair
+            const GenPair q = gp[p];
+            const StepCoef<float>* cp = coef + p * RMAX;
             for (int c = 0; c < NCH; ++c, ++g) {
                 const int st = g & 1;
                 if (st != grp) continue;
                 const uint32_t u = g >> 1;
                 if (u > 0) mbar_wait_bounded(&bar_opfree[st], (u - 1) & 1, a.err);
-                unsigned char* Bh = smem + OFF_B + st * B_BYTES + p * OPB;
-                unsigned char* Bl = smem + OFF_B + st * B_BYTES + (NP + p) * OPB;
-                const int colbase = (kk >> 3) * LBO_B + (kk & 7) * 16;
-                if (!tl.valid[p]) {
-                    for (int rb = 0; rb < nmma; rb += 8) {
-                        *reinterpret_cast<uint4*>(Bh + (rb >> 3) * SBO_B + colbase) = make_uint4(0, 0, 0, 0);
-                        *reinterpret_cast<uint4*>(Bl + (rb >> 3) * SBO_B + colbase) = make_uint4(0, 0, 0, 0);
-                    }
-                } else {
-                    Rec<float> rc;
-                    rc.seed(as, tl.n2[p], tl.m2, c * KC + kk);
-                    const int rp = (tl.mu2[p] - tl.j0) / 2;
-                    const StepCoef<float>* cp = coef + p * RMAX;
-                    for (int rb = 0; rb < nmma; rb += 8) {
-                        float v[8];
+                unsigned char* Bh = smem + OFF_B + st * B_BYTES + p * OPB + (kk >> 3) * LBO_B + (kk & 7) * 16;
+                unsigned char* Bl = Bh + NP * OPB;
+                const int k = c * KC + kk;
+                // seed
+                const float4 tb = t_seed[k];
+                const float Lh = fmaf(q.ps, tb.z, fmaf(q.pc, tb.x, q.Khi));     // exact
+                const float Ll = fmaf(q.ps, tb.w, fmaf(q.pc, tb.y, q.Klo));
+                const float ti = floorf(Lh);
+                int e = (int)ti;
+                const float mant = exp2f((Lh - ti) + Ll);
+                int E = 0;
+                if (e < -60) {
+                    E = (-e - 60 + 119) / 120;
+                    e += 120 * E;
+                }
+                const bool zero = (q.zero_c && k == N - 1) || (q.zero_s && k == 0);
+                float cur = zero ? 0.f : q.sg * mant * __int_as_float((e + 127) << 23);
+                float prev = 0.f;
+                const float2 xs = t_xs[k];
+                const bool fast = __all_sync(0xffffffffu, E == 0);
+                // blocks of 8 rows entirely before my pair's first row: zeros
+                int rb = 0;
+                for (; rb + 8 <= rp && rb < nmma; rb += 8) {
+                    *reinterpret_cast<uint4*>(Bh + (rb >> 3) * SBO_B) = make_uint4(0, 0, 0, 0);
+                    *reinterpret_cast<uint4*>(Bl + (rb >> 3) * SBO_B) = make_uint4(0, 0, 0, 0);
+                }
+                for (; rb < nmma; rb += 8) {
+                    float v[8];
+                    const bool full_blk = (rb >= rp) && (rb + 8 < Lt);   // 8 active rows, each stepped
+                    if (fast && full_blk) {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const StepCoef<float> cf = cp[rb + i];
+                            v[i] = cur;
+                            const float xb = (xs.x - cf.bh) + (xs.y - cf.bl);
+                            const float nxt = fmaf(cf.A * xb, cur, -cf.C * prev);
+                            prev = cur;
+                            cur = nxt;
+                        }
+                    } else {
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
                             const int r = rb + i;
                             if (r < rp || r >= Lt) {
                                 v[i] = 0.f;
                             } else {
-                                v[i] = rc.value();
-                                if (r + 1 < Lt) rc.step(cp[r]);
+                                v[i] = (E == 0) ? cur : 0.f;
+                                if (r + 1 < Lt) {
+                                    const StepCoef<float> cf = cp[r];
+                                    const float xb = (xs.x - cf.bh) + (xs.y - cf.bl);
+                                    const float nxt = fmaf(cf.A * xb, cur, -cf.C * prev);
+                                    prev = cur;
+                                    cur = nxt;
+                                }
                             }
                         }
-                        uint4 h, l;
-                        split2(v[0], v[1], h.x, l.x);
-                        split2(v[2], v[3], h.y, l.y);
-                        split2(v[4], v[5], h.z, l.z);
-                        split2(v[6], v[7], h.w, l.w);
-                        *reinterpret_cast<uint4*>(Bh + (rb >> 3) * SBO_B + colbase) = h;
-                        *reinterpret_cast<uint4*>(Bl + (rb >> 3) * SBO_B + colbase) = l;
+                        if (E > 0 && fabsf(cur) >= 1.099511627776e12f) {   // 2^40
+                            cur *= 7.52316384526264e-37f;                    // 2^-120
+                            prev *= 7.52316384526264e-37f;
+                            --E;
+                        }
                     }
+                    uint4 h, l;
+                    split2(v[0], v[1], h.x, l.x);
+                    split2(v[2], v[3], h.y, l.y);
+                    split2(v[4], v[5], h.z, l.z);
+                    split2(v[6], v[7], h.w, l.w);
+                    *reinterpret_cast<uint4*>(Bh + (rb >> 3) * SBO_B) = h;
+                    *reinterpret_cast<uint4*>(Bl + (rb >> 3) * SBO_B) = l;
                 }
                 fence_proxy_async_smem();
                 __syncwarp();
@@ -436,10 +493,13 @@ static EncodeTiledFn encode_fn() {
 template <int N>
 static cudaError_t launch_n(const BandArgs& a, const void* ws, void* coeffs, cudaStream_t st) {
     CUtensorMap map;
-    const cuuint64_t dims[5] = {(cuuint64_t)N, (cuuint64_t)N, 2, (cuuint64_t)N, (cuuint64_t)a.nfunc};
-    const cuuint64_t strides[4] = {(cuuint64_t)N * 8, (cuuint64_t)N * N * 8, (cuuint64_t)2 * N * N * 8,
+    // tile-major planes of a function: [s][mi][ni/4][k][ni%4]; one chunk of a tile
+    // (16 nodes x 4 consecutive n) is 512 contiguous bytes per function
+    if (!a.ws_tile_major) return cudaErrorInvalidValue;
+    const cuuint64_t dims[5] = {(cuuint64_t)N * NP, (cuuint64_t)N / NP, (cuuint64_t)N, 2, (cuuint64_t)a.nfunc};
+    const cuuint64_t strides[4] = {(cuuint64_t)N * NP * 8, (cuuint64_t)N * N * 8, (cuuint64_t)N * N * N * 8,
                                    (cuuint64_t)2 * N * N * N * 8};
-    const cuuint32_t box[5] = {NP, 1, 1, KC, BM};
+    const cuuint32_t box[5] = {KC * NP, 1, 1, 1, BM};
     const void* base = (const char*)ws + a.ws_group_off * sizeof(float2);
     if (!encode_tensor_map_8b(&map, 5, base, dims, strides, box)) return cudaErrorNotSupported;
     auto kern = contract_tc_kernel<N>;

@@ -50,7 +50,7 @@ struct Cfg {
     static constexpr size_t smem_bytes() {
         return (size_t)(NS + 1) * SLOT * 8 + (size_t)N * 8 * 2 + (size_t)N * 4 + 4 * 8;
     }
-    static constexpr int BLOCKS_PER_SM = (N <= 128) ? 3 : (N <= 256 ? 2 : 1);
+    static constexpr int BLOCKS_PER_SM = (N <= 64) ? 4 : (N <= 128) ? 3 : (N <= 256 ? 2 : 1);
 };
 
 __device__ __forceinline__ void tma_load_3d_hint(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
@@ -309,9 +309,19 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
                 const float scale = wk[k] / (2.f * (float)N * (float)N);
                 const size_t plane_off = a.grid_regular ? a.ws_group_off + (size_t)fb * 2 * N * N * N
                                                         : a.ws_off[a.fidx[fb]];
-                float2* out = ws + plane_off + ((size_t)k * 2 + it.s) * N * N;
                 const int p = it.pb * W + pl;
                 const int ni = (p + N / 2) & (N - 1);
+                // element (mi) of this thread's column ni: [k][s][mi][ni] or, tile-major,
+                // [s][mi][ni/4][k][ni%4] (4 consecutive n of 256 nodes contiguous)
+                float2* out;
+                size_t mstride;
+                if (a.ws_tile_major) {
+                    out = ws + plane_off + (size_t)it.s * N * N * N + (size_t)(ni >> 2) * N * 4 + (size_t)k * 4 + (ni & 3);
+                    mstride = (size_t)N * N;
+                } else {
+                    out = ws + plane_off + ((size_t)k * 2 + it.s) * N * N + ni;
+                    mstride = N;
+                }
                 float sc = ((ni + qb) & 1) ? -scale : scale;     // parity of mi = parity of qb
                 if (it.s) sc = -sc;
                 const bool zero_col = (it.s == 0 && ni == 0);
@@ -321,7 +331,7 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
                     const int mi = (q + N / 2) & (N - 1);
                     float2 val = make_float2(v[qa].x * sc, v[qa].y * sc);
                     if (zero_col || (it.s == 0 && mi == 0)) val = make_float2(0.f, 0.f);
-                    __stcs(out + (size_t)mi * N + ni, val);
+                    __stcs(out + (size_t)mi * mstride, val);
                 }
             } else if (lane == 0 && (warp * 32) >= W * R2) {
                 mbar_arrive_cta(&empty[b]);
@@ -381,12 +391,13 @@ static cudaError_t launch_n(const BandArgs& a, const void* in, void* out, cudaSt
 
 }  // namespace fwd2
 
-bool fft_forward_two_phase_supported(int N, bool fp64) { return !fp64 && (N == 128 || N == 256 || N == 512); }
+bool fft_forward_two_phase_supported(int N, bool fp64) { return !fp64 && (N == 64 || N == 128 || N == 256 || N == 512); }
 
 cudaError_t fft_forward_aux(int N, int device, int* ring, size_t* elems) {
     int G = 0, D = 0, R = 0;
     cudaError_t e;
     switch (N) {
+        case 64: e = fwd2::geometry<64>(device, &G, &D, &R); break;
         case 128: e = fwd2::geometry<128>(device, &G, &D, &R); break;
         case 256: e = fwd2::geometry<256>(device, &G, &D, &R); break;
         case 512: e = fwd2::geometry<512>(device, &G, &D, &R); break;
@@ -403,6 +414,7 @@ cudaError_t fft_forward_aux(int N, int device, int* ring, size_t* elems) {
 cudaError_t launch_fft_forward_two_phase(const BandArgs& a, const void* grid, void* ws, cudaStream_t st) {
     if (a.nfunc <= 0) return cudaSuccess;
     switch (a.N) {
+        case 64: return fwd2::launch_n<64>(a, grid, ws, st);
         case 128: return fwd2::launch_n<128>(a, grid, ws, st);
         case 256: return fwd2::launch_n<256>(a, grid, ws, st);
         case 512: return fwd2::launch_n<512>(a, grid, ws, st);

@@ -41,26 +41,43 @@ __device__ __forceinline__ StepCoef<T> step_coef(int J, int n2, int m2) {
     return c;
 }
 
-// log2 |d^mu_{nm}(beta_k)| and its sign (Rodrigues-type formula at l = mu).
-__device__ __forceinline__ double seed_log2(const BandArgs& a, int n2, int m2, int k, double* sgn) {
+// Seed of the pair (n, m) at l = mu = max(|n|, |m|) (Rodrigues-type formula of
+// Sec. 3 evaluated there):  d^mu_{nm}(beta) = sg * 2^K * cos(beta/2)^pc * sin(beta/2)^ps
+// with K = log2 sqrt((2 mu)! / ((mu + o)! (mu - o)!)), o the index other than the
+// one at +-mu.  Doubled indices throughout.
+struct SeedParams {
+    double K;
+    int pc, ps;
+    double sg;
+};
+
+__device__ __forceinline__ SeedParams seed_params(const double* lf2, int n2, int m2) {
     const int mu2 = max(abs(n2), abs(m2));
-    int other, pc, ps;
-    double sg = 1.0;
+    SeedParams p;
+    int other;
+    p.sg = 1.0;
     if (abs(n2) == mu2 && (n2 > 0 || mu2 == 0)) {
-        other = m2; pc = (mu2 + m2) / 2; ps = (mu2 - m2) / 2;
-        if (((mu2 - m2) / 2) & 1) sg = -1.0;
+        other = m2; p.pc = (mu2 + m2) / 2; p.ps = (mu2 - m2) / 2;
+        if (((mu2 - m2) / 2) & 1) p.sg = -1.0;
     } else if (n2 == -mu2) {
-        other = m2; pc = (mu2 - m2) / 2; ps = (mu2 + m2) / 2;
+        other = m2; p.pc = (mu2 - m2) / 2; p.ps = (mu2 + m2) / 2;
     } else if (m2 == mu2) {
-        other = n2; pc = (mu2 + n2) / 2; ps = (mu2 - n2) / 2;
+        other = n2; p.pc = (mu2 + n2) / 2; p.ps = (mu2 - n2) / 2;
     } else {
-        other = n2; pc = (mu2 - n2) / 2; ps = (mu2 + n2) / 2;
-        if (((mu2 + n2) / 2) & 1) sg = -1.0;
+        other = n2; p.pc = (mu2 - n2) / 2; p.ps = (mu2 + n2) / 2;
+        if (((mu2 + n2) / 2) & 1) p.sg = -1.0;
     }
-    double L = 0.5 * (a.lf2[mu2] - a.lf2[(mu2 + other) / 2] - a.lf2[(mu2 - other) / 2]);
-    if (pc) L += (double)pc * a.log2c[k];
-    if (ps) L += (double)ps * a.log2s[k];
-    *sgn = sg;
+    p.K = 0.5 * (lf2[mu2] - lf2[(mu2 + other) / 2] - lf2[(mu2 - other) / 2]);
+    return p;
+}
+
+// log2 |d^mu_{nm}(beta_k)| and its sign, in FP64.
+__device__ __forceinline__ double seed_log2(const BandArgs& a, int n2, int m2, int k, double* sgn) {
+    const SeedParams sp = seed_params(a.lf2, n2, m2);
+    double L = sp.K;
+    if (sp.pc) L += (double)sp.pc * a.log2c[k];
+    if (sp.ps) L += (double)sp.ps * a.log2s[k];
+    *sgn = sp.sg;
     return L;
 }
 

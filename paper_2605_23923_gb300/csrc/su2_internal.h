@@ -14,8 +14,8 @@ namespace su2 {
 // Stage 1: 2-D DFT over (alpha, gamma) for every beta node (forward), and the
 // inverse torus synthesis.  `fp64` selects complex128 data.
 cudaError_t launch_fft_forward(const BandArgs& a, bool fp64, const void* grid, void* ws, cudaStream_t st);
-// Two-phase complex64 forward DFT (N = 128, 256, 512): its scratch ring (plane
-// slots and size in complex elements, for the plan's workspace) and launch.
+// Two-phase complex64 forward DFT (N = 64, 128, 256, 512): its scratch ring
+// (plane slots and size in complex elements, for the plan's workspace) and launch.
 bool fft_forward_two_phase_supported(int N, bool fp64);
 cudaError_t fft_forward_aux(int N, int device, int* ring, size_t* elems);
 cudaError_t launch_fft_forward_two_phase(const BandArgs& a, const void* grid, void* ws, cudaStream_t st);

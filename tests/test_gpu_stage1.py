@@ -44,15 +44,23 @@ def expected_planes(f, k):
     return out
 
 
-def check_planes(plan, ws, f, fi, ks):
+def read_plane(c, base, N, k, s, tile_major):
+    if not tile_major:
+        o = base + (2 * k + s) * N * N
+        return c[o:o + N * N].cpu().numpy().astype(np.complex128).reshape(N, N)
+    # [s][mi][ni/4][k][ni%4]
+    blk = c[base + s * N ** 3: base + (s + 1) * N ** 3].reshape(N, N // 4, N, 4)
+    return blk[:, :, k, :].reshape(N, N).cpu().numpy().astype(np.complex128)
+
+
+def check_planes(plan, ws, f, fi, ks, tile_major=False):
     N = f.shape[0]
     c = ws.view(torch.complex64)
     base = plan.plane_offsets[fi]
     worst = scale = 0.0
     for k in ks:
         for s, ref in enumerate(expected_planes(f, k)):
-            o = base + (2 * k + s) * N * N
-            got = c[o:o + N * N].cpu().numpy().astype(np.complex128).reshape(N, N)
+            got = read_plane(c, base, N, k, s, tile_major)
             worst = max(worst, float(np.max(np.abs(got - ref))))
             scale = max(scale, float(np.max(np.abs(ref))))
             if s == 0:
@@ -115,3 +123,16 @@ def test_stage1_workspace_only_16_byte_aligned(su2):
     plan.sync_status()
     for fi, g in enumerate(grids):
         check_planes(plan, ws, g.astype(np.complex128), fi, [0, 7, N // 2, N - 1])
+
+
+@pytest.mark.parametrize("N,B", [(64, 3), (256, 2)])
+def test_stage1_planes_tensor_core_layout(su2, N, B):
+    """Plans of the tensor-core path keep the planes tile-major."""
+    rng = np.random.default_rng(50 + N)
+    grids = [I.draw_grid_gaussian((N, N, N), rng).astype(np.complex64) for _ in range(B)]
+    plan = su2.Plan(N=N, batch=B, dtype="c64", algo="tc_bf16x3")
+    x = torch.from_numpy(np.concatenate([g.reshape(-1) for g in grids])).cuda()
+    ws = plan.forward_stage1(x)
+    plan.sync_status()
+    for fi, g in enumerate(grids):
+        check_planes(plan, ws, g.astype(np.complex128), fi, [0, 1, N // 2, N - 1], tile_major=True)
