@@ -61,12 +61,20 @@ constexpr int OFF_COEF = OFF_B + 2 * B_BYTES;
 constexpr int OFF_TAB = OFF_COEF + 2 * NP * RMAX * (int)sizeof(StepCoef<float>);
 // seed32 (float4) + lf2 (double) + xsplit (float2) + seed parameters of the pairs
 struct GenPair { float Khi, Klo, pc, ps, sg; int zero_c, zero_s, pad; };
-constexpr int TAB_BYTES = NMAX * 16 + NMAX * 8 + NMAX * 8 + 2 * NP * (int)sizeof(GenPair);
+constexpr int TAB_BYTES = NMAX * 16 + NMAX * 8 + NMAX * 8 + 2 * NP * (int)sizeof(GenPair) + NMAX * 4;
 constexpr int OFF_BAR = OFF_TAB + TAB_BYTES;
-constexpr int NBAR = 12;
+constexpr int NBAR = 14;
 constexpr int SMEM_BYTES = OFF_BAR + NBAR * 8 + 16;
 static_assert(SMEM_BYTES <= 232448, "shared memory budget");
-constexpr uint32_t TMEM_COLS = 512;         // 4 pairs x 128 columns
+constexpr uint32_t TMEM_COLS = 512;         // 4 pairs x 128 columns, or two halves of 4 x 64
+// Accumulator placement: a tile with at most 64 rows of l ("small") takes one
+// half of tensor memory (pairs 64 columns apart), alternating halves, so its
+// MMAs overlap the epilogue of the previous tile; a larger tile takes both.
+__device__ __forceinline__ void acc_place(int nmma, int& nexth, int& h0, bool& big) {
+    big = nmma > 64;
+    h0 = big ? 0 : nexth;
+    if (!big) nexth ^= 1;
+}
 
 __device__ __forceinline__ int a_off(int row, int kk) {
     return (row >> 3) * SBO_A + (kk >> 3) * LBO_A + (row & 7) * 16 + (kk & 7) * 2;
@@ -148,19 +156,21 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
     uint64_t* bar_afull = bars + 4;    // [2] A operands written          (count N_CONV)
     uint64_t* bar_bfull = bars + 6;    // [2] B operands written          (count 2)
     uint64_t* bar_opfree = bars + 8;   // [2] MMAs of the stage done      (tcgen05.commit)
-    uint64_t* bar_accfull = bars + 10; //     accumulators of a tile final (tcgen05.commit)
-    uint64_t* bar_accfree = bars + 11; //     epilogue drained TMEM        (count 4)
+    uint64_t* bar_accfull = bars + 10; // [2] accumulators of a tile in half h final (tcgen05.commit)
+    uint64_t* bar_hfree = bars + 12;   // [2] epilogue drained half h      (count 4)
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + NBAR);
     float4* t_seed = reinterpret_cast<float4*>(smem + OFF_TAB);
     double* t_lf2 = reinterpret_cast<double*>(t_seed + NMAX);
     float2* t_xs = reinterpret_cast<float2*>(t_lf2 + NMAX);
     GenPair* t_gp = reinterpret_cast<GenPair*>(t_xs + NMAX);      // [2 groups][NP]
+    uint32_t* t_rowoff = reinterpret_cast<uint32_t*>(t_gp + 2 * NP); // J(J+1)(2J+1)/6, J = 2l
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     for (int t = tid; t < N; t += THREADS) {
         t_seed[t] = a.seed32[t];
         t_lf2[t] = a.lf2[t];
         t_xs[t] = a.xsplit[t];
+        t_rowoff[t] = (uint32_t)block_offset(t);
     }
     if (warp == W_MMA) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -175,8 +185,10 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
             mbar_init(&bar_bfull[i], 2);
             mbar_init(&bar_opfree[i], 1);
         }
-        mbar_init(bar_accfull, 1);
-        mbar_init(bar_accfree, 4);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&bar_accfull[i], 1);
+            mbar_init(&bar_hfree[i], 4);
+        }
         mbar_fence_init();
     }
     tc_fence_before();
@@ -211,13 +223,25 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
     } else if (warp == W_MMA) {
         // ------------------------------------------------------------------ MMA
         if (lane == 0) {
-            uint32_t g = 0, ti = 0;
+            uint32_t g = 0, uses[2] = {0, 0};
+            int nexth = 0;
             for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
                 Tile<NP> tl;
                 tl.decode(N, item / nbb);
                 if (!tl.any) continue;
-                const uint32_t idesc = instr_desc((tl.L + 15) & ~15);
-                if (ti > 0) mbar_wait_bounded(bar_accfree, (ti - 1) & 1, a.err);
+                const int nmma = (tl.L + 15) & ~15;
+                const uint32_t idesc = instr_desc(nmma);
+                int h0;
+                bool big;
+                acc_place(nmma, nexth, h0, big);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (h != h0 && !big) continue;
+                    if (uses[h] > 0) mbar_wait_bounded(&bar_hfree[h], (uses[h] - 1) & 1, a.err);
+                    ++uses[h];
+                }
+                const uint32_t base = taddr + (uint32_t)(h0 * 256);
+                const uint32_t pstride = big ? 128u : 64u;
                 tc_fence_after();
                 for (int c = 0; c < NCH; ++c, ++g) {
                     const int st = g & 1;
@@ -230,7 +254,7 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
 #pragma unroll
                     for (int p = 0; p < NP; ++p) {
                         if (!tl.valid[p]) continue;
-                        const uint32_t d = taddr + (uint32_t)(p * 128);
+                        const uint32_t d = base + (uint32_t)p * pstride;
                         const uint64_t ah = smem_desc(Ab + p * OPA, LBO_A, SBO_A);
                         const uint64_t al = smem_desc(Ab + (NP + p) * OPA, LBO_A, SBO_A);
                         const uint64_t bh = smem_desc(Bb + p * OPB, LBO_B, SBO_B);
@@ -241,8 +265,7 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
                     }
                     mma_commit(&bar_opfree[st]);
                 }
-                mma_commit(bar_accfull);
-                ++ti;
+                mma_commit(&bar_accfull[h0]);
             }
         }
     } else if ((warp >= W_CONV && warp < W_CONV + 4) || warp == W_CONV2 || warp == W_CONV2 + 1) {
@@ -411,15 +434,22 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
     } else if (warp >= W_EPI && warp < W_EPI + 4) {
         // ------------------------------------------------------------------ epilogue
         const int q = warp - W_EPI;                          // TMEM lane quadrant (warp % 4)
-        uint32_t ti = 0;
+        uint32_t commits[2] = {0, 0};
+        int nexth = 0;
         for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
             Tile<NP> tl;
             tl.decode(N, item / nbb);
             if (!tl.any) continue;
             const int bb = item % nbb;
             const int Lt = tl.L, nmma = (Lt + 15) & ~15;
-            mbar_wait_bounded(bar_accfull, ti & 1, a.err);
+            int h0;
+            bool big;
+            acc_place(nmma, nexth, h0, big);
+            mbar_wait_bounded(&bar_accfull[h0], commits[h0] & 1, a.err);
+            ++commits[h0];
             tc_fence_after();
+            const uint32_t base = taddr + ((uint32_t)(32 * q) << 16) + (uint32_t)(h0 * 256);
+            const uint32_t pstride = big ? 128u : 64u;
             // After the TMEM load lane l holds row 32q + l (function 16q + l/2, re or im)
             // for the 4 pairs.  For the stores, lane t takes function 16q + 8h + t/4 and
             // pair t%4 (h = 0, 1), so 4 adjacent lanes write 4 consecutive n.
@@ -439,13 +469,13 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
                 uint32_t rv[NP][16];
 #pragma unroll
                 for (int pp = 0; pp < NP; ++pp)
-                    tmem_ld16(taddr + ((uint32_t)(32 * q) << 16) + (uint32_t)(pp * 128 + cc), rv[pp]);
+                    tmem_ld16(base + (uint32_t)pp * pstride + (uint32_t)cc, rv[pp]);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int r = cc + j;
                     const int J = tl.j0 + 2 * r;
-                    const size_t rowbase = block_offset(J) + (size_t)((tl.m2 + J) / 2) * (J + 1);
+                    const size_t rowbase = (size_t)t_rowoff[J < N ? J : N - 1] + (size_t)((tl.m2 + J) / 2) * (J + 1);
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const int src = 16 * h + 2 * (lane >> 2);      // lane holding re of my function
@@ -463,8 +493,10 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(bar_accfree);
-            ++ti;
+            if (lane == 0) {
+                mbar_arrive(&bar_hfree[h0]);
+                if (big) mbar_arrive(&bar_hfree[1]);
+            }
         }
     }
     tc_fence_before();
