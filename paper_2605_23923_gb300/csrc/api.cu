@@ -435,7 +435,8 @@ static su2_status run_transpose(su2_plan_t plan, su2::TransposeMode mode, const 
     cudaStream_t st = (cudaStream_t)stream;
     const bool fp64 = plan->dtype == SU2_C128;
     for (auto& kv : plan->bands) {
-        const su2::BandArgs a = band_args(plan, kv.second);
+        su2::BandArgs a = band_args(plan, kv.second);
+        a.ws_tile_major = fp64 ? 0 : 1;      // complex64 synthesis planes are tile-major
         cudaError_t e = su2::launch_contract_transpose(a, fp64, mode, coeffs, ws, st);
         if (e == cudaSuccess) e = su2::launch_fft_inverse(a, fp64, ws, grid, st);
         if (e != cudaSuccess) return from_cuda(e);

@@ -26,6 +26,8 @@
 // acc[l][b] += d[l][k] * F2[k][b].
 #include <math.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "recurrence.cuh"
 #include "su2_internal.h"
@@ -49,7 +51,8 @@ struct FwdCfg {
     static constexpr int THREADS = NB * (LW / ML) * (BT / MB);
     static constexpr int LDD = LW + 4;
     static size_t smem_bytes(int N) {
-        return sizeof(StepCoef<T>) * NB * (N / 2) + sizeof(T) * NB * KC * LDD + sizeof(cplx<T>) * KC * NB * BT;
+        return sizeof(StepCoef<T>) * NB * (N / 2) + sizeof(T) * NB * KC * LDD + sizeof(cplx<T>) * KC * NB * BT +
+               sizeof(SeedPair) * NB;
     }
 };
 
@@ -74,7 +77,10 @@ contract_fwd(BandArgs a, const cplx<T>* __restrict__ F2, cplx<T>* __restrict__ c
     StepCoef<T>* coef = reinterpret_cast<StepCoef<T>*>(smem_raw);                 // [NB][RS]
     T* Dsm = reinterpret_cast<T*>(coef + NB * RS);                                 // [NB][KC][LDD]
     Cx* Fsm = reinterpret_cast<Cx*>(Dsm + NB * KC * LDD);                          // [KC][NB][BT]
+    SeedPair* spair = reinterpret_cast<SeedPair*>(Fsm + KC * NB * BT);            // [NB] (FP32 seeds)
     const int tid = threadIdx.x;
+    constexpr bool F32 = std::is_same<T, float>::value;
+    if (F32 && tid < NB) spair[tid] = make_seed_pair(a.lf2, tl.n2[tid], tl.m2);
 
     // Step coefficients for rows r in [0, r_end - 1) of every pair.
     for (int idx = tid; idx < NB * (r_end - 1); idx += THREADS) {
@@ -100,13 +106,26 @@ contract_fwd(BandArgs a, const cplx<T>* __restrict__ F2, cplx<T>* __restrict__ c
             // ---- recurrence for (pair p, node k), rows r0 .. r0+LW-1 into shared memory
             const int p = tid / KC, kk = tid % KC, k = k0 + kk;
             T* drow = Dsm + (p * KC + kk) * LDD;
-            if (!tl.valid[p] || k >= N) {
+            const bool live = tl.valid[p] && k < N;
+            Rec<T> rc;
+            bool fast = false;
+            if constexpr (F32) {
+                const int kc = live ? k : 0;
+                rc.seed32(spair[p], a.seed32[kc], a.xsplit[kc], kc, N);
+                if (!live) { rc.cur = 0.f; rc.E = 0; }
+                fast = __all_sync(0xffffffffu, rc.E == 0);       // generator threads are whole warps
+            } else if (live) {
+                rc.seed(a, tl.n2[p], tl.m2, k);
+            }
+            if (!live) {
                 for (int rb = 0; rb < LW; rb += 4) { const T z[4] = {T(0), T(0), T(0), T(0)}; store4<T>(drow + rb, z); }
             } else {
-                Rec<T> rc;
-                rc.seed(a, tl.n2[p], tl.m2, k);
+                auto adv = [&](const StepCoef<T>& c) {
+                    if constexpr (F32) { if (fast) rc.step_fast(c); else rc.step(c); }
+                    else rc.step(c);
+                };
                 int r = (tl.mu2[p] - tl.j0) / 2;      // row of the seed
-                while (r < r0) { rc.step(coef[p * RS + r]); ++r; }
+                while (r < r0) { adv(coef[p * RS + r]); ++r; }
                 for (int rb = 0; rb < LW; rb += 4) {
                     T v[4];
 #pragma unroll
@@ -116,7 +135,7 @@ contract_fwd(BandArgs a, const cplx<T>* __restrict__ F2, cplx<T>* __restrict__ c
                             v[i] = T(0);
                         } else {
                             v[i] = rc.value();
-                            if (rr + 1 < r_end) { rc.step(coef[p * RS + rr]); r = rr + 1; }
+                            if (rr + 1 < r_end) { adv(coef[p * RS + rr]); r = rr + 1; }
                         }
                     }
                     store4<T>(drow + rb, v);
@@ -197,7 +216,8 @@ struct TrCfg {
     static constexpr int THREADS = NB * (KC / MK) * (BT / MB);
     static size_t smem_bytes(int N) {
         const int RS = N / 2;
-        return sizeof(StepCoef<T>) * NB * RS + sizeof(T) * NB * RS * KC + sizeof(cplx<T>) * NB * RS * BT;
+        return sizeof(StepCoef<T>) * NB * RS + sizeof(T) * NB * RS * KC + sizeof(cplx<T>) * NB * RS * BT +
+               sizeof(SeedPair) * NB;
     }
 };
 
@@ -220,7 +240,10 @@ contract_tr(BandArgs a, int mode, const cplx<T>* __restrict__ coeffs, cplx<T>* _
     StepCoef<T>* coef = reinterpret_cast<StepCoef<T>*>(smem_raw);   // [NB][RS]
     T* Dsm = reinterpret_cast<T*>(coef + NB * RS);                   // [NB][RS][KC]
     Cx* Csm = reinterpret_cast<Cx*>(Dsm + NB * RS * KC);             // [NB][RS][BT]
+    SeedPair* spair = reinterpret_cast<SeedPair*>(Csm + NB * RS * BT); // [NB] (FP32 seeds)
     const int tid = threadIdx.x;
+    constexpr bool F32 = std::is_same<T, float>::value;
+    if (F32 && tid < NB) spair[tid] = make_seed_pair(a.lf2, tl.n2[tid], tl.m2);
 
     for (int idx = tid; idx < NB * (L - 1); idx += THREADS) {
         const int p = idx % NB, r = idx / NB;
@@ -252,16 +275,39 @@ contract_tr(BandArgs a, int mode, const cplx<T>* __restrict__ coeffs, cplx<T>* _
         if (tid < NB * KC) {
             const int p = tid / KC, kk = tid % KC, k = k0 + kk;
             T* dcol = Dsm + p * RS * KC + kk;
-            if (!tl.valid[p] || k >= N) {
+            const bool live = tl.valid[p] && k < N;
+            Rec<T> rc;
+            bool fast = false;
+            if constexpr (F32) {
+                const int kc = live ? k : 0;
+                rc.seed32(spair[p], a.seed32[kc], a.xsplit[kc], kc, N);
+                if (!live) { rc.cur = 0.f; rc.E = 0; }
+                fast = __all_sync(0xffffffffu, rc.E == 0);       // generator threads are whole warps
+            } else if (live) {
+                rc.seed(a, tl.n2[p], tl.m2, k);
+            }
+            if (!live) {
                 for (int r = 0; r < L; ++r) dcol[r * KC] = T(0);
             } else {
-                Rec<T> rc;
-                rc.seed(a, tl.n2[p], tl.m2, k);
                 const int rs = (tl.mu2[p] - tl.j0) / 2;
                 for (int r = 0; r < rs; ++r) dcol[r * KC] = T(0);
-                for (int r = rs; r < L; ++r) {
-                    dcol[r * KC] = rc.value();
-                    if (r + 1 < L) rc.step(coef[p * RS + r]);
+                if constexpr (F32) {
+                    if (fast) {
+                        for (int r = rs; r < L; ++r) {
+                            dcol[r * KC] = rc.cur;
+                            if (r + 1 < L) rc.step_fast(coef[p * RS + r]);
+                        }
+                    } else {
+                        for (int r = rs; r < L; ++r) {
+                            dcol[r * KC] = rc.value();
+                            if (r + 1 < L) rc.step(coef[p * RS + r]);
+                        }
+                    }
+                } else {
+                    for (int r = rs; r < L; ++r) {
+                        dcol[r * KC] = rc.value();
+                        if (r + 1 < L) rc.step(coef[p * RS + r]);
+                    }
                 }
             }
         }
@@ -308,6 +354,148 @@ contract_tr(BandArgs a, int mode, const cplx<T>* __restrict__ coeffs, cplx<T>* _
 }
 
 // ---------------------------------------------------------------------------
+// Transposed contraction, complex64 (synthesis / adjoint), fused form.
+// A CTA owns a tile (sector, m, NB = 4 consecutive n) and BT = 8 functions;
+// thread (g, h) runs the recurrence chains of pairs 2h, 2h+1 at the two nodes
+// k = 2g, 2g+1 of the current pass and accumulates, while walking l,
+//     acc[node][pair][b] += d^l_{nm}(beta_k) * Cw[l][pair][b],
+// where Cw = wl(l) i^{m-n} c(l)_{mn} is kept in shared memory for the whole l
+// range (one broadcast row per l).  No d values are stored.  Output: the
+// workspace planes tile-major, [s][mi][ni/4][k][ni%4], so that the two
+// threads of a node group write one 32-byte sector and a warp 512 bytes.
+// ---------------------------------------------------------------------------
+namespace tr32 {
+constexpr int NB = 4, BT = 8;
+template <int N> struct Cfg {
+    static constexpr int THREADS = N < 256 ? N : 256;        // 2 threads per node pair-group
+    static constexpr int NODES = THREADS;                     // nodes per pass (2 per node group)
+    static constexpr int PASSES = N / NODES;
+    static constexpr int RS = N / 2;
+    static constexpr size_t smem_bytes() {
+        return sizeof(StepCoef<float>) * NB * RS + sizeof(float2) * RS * NB * BT + sizeof(SeedPair) * NB + 16 * NB;
+    }
+};
+}  // namespace tr32
+
+template <int N>
+__global__ void __launch_bounds__(tr32::Cfg<N>::THREADS)
+contract_tr32(BandArgs a, int mode, const float2* __restrict__ coeffs, float2* __restrict__ G) {
+    using namespace tr32;
+    using P = Cfg<N>;
+    constexpr int RS = P::RS;
+    Tile<NB> tl;
+    tl.decode(N, blockIdx.x);
+    if (!tl.any) return;
+    const int bb = blockIdx.y;
+    const int L = tl.L;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    StepCoef<float>* coef = reinterpret_cast<StepCoef<float>*>(smem_raw);   // [NB][RS]
+    float2* Csm = reinterpret_cast<float2*>(coef + NB * RS);               // [RS][NB][BT]
+    SeedPair* spair = reinterpret_cast<SeedPair*>(Csm + RS * NB * BT);      // [NB]
+    int* rstart = reinterpret_cast<int*>(spair + NB);                       // [NB] first row of each pair
+    const int tid = threadIdx.x;
+
+    for (int idx = tid; idx < NB * (L - 1); idx += P::THREADS) {
+        const int p = idx % NB, r = idx / NB;
+        const int J = tl.j0 + 2 * r;
+        if (J >= tl.mu2[p]) coef[p * RS + r] = step_coef<float>(J, tl.n2[p], tl.m2);
+    }
+    for (int idx = tid; idx < L * NB * BT; idx += P::THREADS) {
+        const int b = idx % BT, p = (idx / BT) % NB, r = idx / (BT * NB);
+        const int J = tl.j0 + 2 * r;
+        const int fb = bb * BT + b;
+        float2 v = make_float2(0.f, 0.f);
+        if (tl.valid[p] && J >= tl.mu2[p] && fb < a.nfunc) {
+            const int f = a.fidx[fb];
+            const size_t ci = block_offset(J) + (size_t)((tl.m2 + J) / 2) * (J + 1) + (tl.n2[p] + J) / 2;
+            v = cmul_ipow(coeffs[a.coeff_off[f] + ci], (tl.m2 - tl.n2[p]) / 2);
+            if (mode == 0) v = cscale(v, (float)(J + 1));
+        }
+        Csm[(r * NB + p) * BT + b] = v;
+    }
+    if (tid < NB) {
+        spair[tid] = make_seed_pair(a.lf2, tl.n2[tid], tl.m2);
+        rstart[tid] = tl.valid[tid] ? (tl.mu2[tid] - tl.j0) / 2 : L;
+    }
+    __syncthreads();
+
+    const int h = tid & 1, gidx = tid >> 1;
+    const int rs0 = rstart[2 * h], rs1 = rstart[2 * h + 1];
+    const SeedPair q0 = spair[2 * h], q1 = spair[2 * h + 1];
+    const StepCoef<float>* c0p = coef + (2 * h) * RS;
+    const StepCoef<float>* c1p = coef + (2 * h + 1) * RS;
+    const float inv2n2 = 1.f / (2.f * (float)N * (float)N);
+    const int ni0 = tl.nb * NB + 2 * h;
+
+    for (int pass = 0; pass < P::PASSES; ++pass) {
+        const int ka = pass * P::NODES + 2 * gidx;           // nodes ka, ka + 1
+        Rec<float> ch[2][2];                                  // [node][pair]
+#pragma unroll
+        for (int nd = 0; nd < 2; ++nd) {
+            const int k = ka + nd;
+            ch[nd][0].seed32(q0, a.seed32[k], a.xsplit[k], k, N);
+            ch[nd][1].seed32(q1, a.seed32[k], a.xsplit[k], k, N);
+        }
+        constexpr unsigned mask = P::THREADS >= 32 ? 0xffffffffu : ((1u << P::THREADS) - 1u);
+        const bool fast = __all_sync(mask, (ch[0][0].E | ch[0][1].E | ch[1][0].E | ch[1][1].E) == 0);
+        float2 acc[2][2][BT];
+#pragma unroll
+        for (int nd = 0; nd < 2; ++nd)
+#pragma unroll
+            for (int pp = 0; pp < 2; ++pp)
+#pragma unroll
+                for (int b = 0; b < BT; ++b) acc[nd][pp][b] = make_float2(0.f, 0.f);
+
+        for (int r = min(rs0, rs1); r < L; ++r) {
+            const float4* crow = reinterpret_cast<const float4*>(Csm + (r * NB + 2 * h) * BT);
+#pragma unroll
+            for (int pp = 0; pp < 2; ++pp) {
+                if (r < (pp ? rs1 : rs0)) continue;           // uniform across the CTA
+                float2 cv[BT];
+#pragma unroll
+                for (int b2 = 0; b2 < BT / 2; ++b2) {
+                    const float4 t = crow[pp * (BT / 2) + b2];
+                    cv[2 * b2] = make_float2(t.x, t.y);
+                    cv[2 * b2 + 1] = make_float2(t.z, t.w);
+                }
+                const StepCoef<float> cf = (pp ? c1p : c0p)[r];
+#pragma unroll
+                for (int nd = 0; nd < 2; ++nd) {
+                    Rec<float>& rc = ch[nd][pp];
+                    const float dv = fast ? rc.cur : rc.value();
+#pragma unroll
+                    for (int b = 0; b < BT; ++b) {
+                        acc[nd][pp][b].x = fmaf(dv, cv[b].x, acc[nd][pp][b].x);
+                        acc[nd][pp][b].y = fmaf(dv, cv[b].y, acc[nd][pp][b].y);
+                    }
+                    if (r + 1 < L) {
+                        if (fast) rc.step_fast(cf);
+                        else rc.step(cf);
+                    }
+                }
+            }
+        }
+        // store: element (k, s, mi, ni) at s N^3 + mi N^2 + (ni/4) 4N + 4k + ni%4
+#pragma unroll
+        for (int nd = 0; nd < 2; ++nd) {
+            const int k = ka + nd;
+            const float rho = (mode == 1) ? a.w32[k] * inv2n2 : 1.f;
+#pragma unroll
+            for (int b = 0; b < BT; ++b) {
+                const int fb = bb * BT + b;
+                if (fb >= a.nfunc) continue;
+                const int f = a.fidx[fb];
+                float4* dst = reinterpret_cast<float4*>(G + a.ws_off[f] + (size_t)tl.s * N * N * N +
+                                                        (size_t)tl.mi * N * N + (size_t)(ni0 >> 2) * 4 * N +
+                                                        (size_t)4 * k + (ni0 & 3));
+                *dst = make_float4(acc[nd][0][b].x * rho, acc[nd][0][b].y * rho, acc[nd][1][b].x * rho,
+                                   acc[nd][1][b].y * rho);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
 template <typename T, int NB, int BT, int KC, int LW, int ML, int MB>
@@ -327,6 +515,8 @@ static cudaError_t launch_fwd_t(const BandArgs& a, const void* ws, void* coeffs,
 cudaError_t launch_contract_forward(const BandArgs& a, bool fp64, const void* ws, void* coeffs, cudaStream_t st) {
     if (a.nfunc <= 0) return cudaSuccess;
     if (fp64) return launch_fwd_t<double, 4, 8, 32, 64, 4, 2>(a, ws, coeffs, st);
+    // small batches: 8 functions per CTA, so that no FMA lane works on padding
+    if (a.nfunc <= 8) return launch_fwd_t<float, 4, 8, 16, 128, 8, 4>(a, ws, coeffs, st);
     return launch_fwd_t<float, 4, 16, 32, 128, 8, 4>(a, ws, coeffs, st);
 }
 
@@ -343,12 +533,35 @@ static cudaError_t launch_tr_t(const BandArgs& a, int mode, const void* coeffs, 
     return cudaGetLastError();
 }
 
+template <int N>
+static cudaError_t launch_tr32_n(const BandArgs& a, int mode, const void* coeffs, void* ws, cudaStream_t st) {
+    using P = tr32::Cfg<N>;
+    auto kern = contract_tr32<N>;
+    const size_t smem = P::smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 g(2 * N * (N / tr32::NB), (a.nfunc + tr32::BT - 1) / tr32::BT, 1);
+    kern<<<g, P::THREADS, smem, st>>>(a, mode, (const float2*)coeffs, (float2*)ws);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_contract_transpose(const BandArgs& a, bool fp64, TransposeMode mode, const void* coeffs,
                                       void* ws, cudaStream_t st) {
     if (a.nfunc <= 0) return cudaSuccess;
     const int m = (mode == TransposeMode::Synthesis) ? 0 : 1;
     if (fp64) return launch_tr_t<double, 4, 4, 16, 2, 2>(a, m, coeffs, ws, st);
-    return launch_tr_t<float, 4, 8, 16, 2, 2>(a, m, coeffs, ws, st);
+    if (!a.ws_tile_major) return cudaErrorInvalidValue;      // the complex64 planes are tile-major here
+    switch (a.N) {
+        case 4: return launch_tr32_n<4>(a, m, coeffs, ws, st);
+        case 8: return launch_tr32_n<8>(a, m, coeffs, ws, st);
+        case 16: return launch_tr32_n<16>(a, m, coeffs, ws, st);
+        case 32: return launch_tr32_n<32>(a, m, coeffs, ws, st);
+        case 64: return launch_tr32_n<64>(a, m, coeffs, ws, st);
+        case 128: return launch_tr32_n<128>(a, m, coeffs, ws, st);
+        case 256: return launch_tr32_n<256>(a, m, coeffs, ws, st);
+        case 512: return launch_tr32_n<512>(a, m, coeffs, ws, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace su2

@@ -60,8 +60,7 @@ constexpr int OFF_B = OFF_A + ((2 * A_BYTES + 127) / 128) * 128;
 constexpr int OFF_COEF = OFF_B + 2 * B_BYTES;
 constexpr int OFF_TAB = OFF_COEF + 2 * NP * RMAX * (int)sizeof(StepCoef<float>);
 // seed32 (float4) + lf2 (double) + xsplit (float2) + seed parameters of the pairs
-struct GenPair { float Khi, Klo, pc, ps, sg; int zero_c, zero_s, pad; };
-constexpr int TAB_BYTES = NMAX * 16 + NMAX * 8 + NMAX * 8 + 2 * NP * (int)sizeof(GenPair) + NMAX * 4;
+constexpr int TAB_BYTES = NMAX * 16 + NMAX * 8 + NMAX * 8 + 2 * NP * (int)sizeof(SeedPair) + NMAX * 4;
 constexpr int OFF_BAR = OFF_TAB + TAB_BYTES;
 constexpr int NBAR = 14;
 constexpr int SMEM_BYTES = OFF_BAR + NBAR * 8 + 16;
@@ -162,7 +161,7 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
     float4* t_seed = reinterpret_cast<float4*>(smem + OFF_TAB);
     double* t_lf2 = reinterpret_cast<double*>(t_seed + NMAX);
     float2* t_xs = reinterpret_cast<float2*>(t_lf2 + NMAX);
-    GenPair* t_gp = reinterpret_cast<GenPair*>(t_xs + NMAX);      // [2 groups][NP]
+    SeedPair* t_gp = reinterpret_cast<SeedPair*>(t_xs + NMAX);      // [2 groups][NP]
     uint32_t* t_rowoff = reinterpret_cast<uint32_t*>(t_gp + 2 * NP); // J(J+1)(2J+1)/6, J = 2l
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -320,7 +319,7 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
         const int gt = tid - W_GEN * 32 - grp * 64;        // 0..63
         const int p = gt >> 4, kk = gt & 15;
         StepCoef<float>* coef = reinterpret_cast<StepCoef<float>*>(smem + OFF_COEF) + grp * NP * RMAX;
-        GenPair* gp = t_gp + grp * NP;
+        SeedPair* gp = t_gp + grp * NP;
         uint32_t g = 0;
         for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
             Tile<NP> tl;
@@ -333,23 +332,11 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
                 const int J = tl.j0 + 2 * r;
                 if (J >= tl.mu2[pp]) coef[pp * RMAX + r] = step_coef<float>(J, tl.n2[pp], tl.m2);
             }
-            if (gt < NP) {
-                const SeedParams sp = seed_params(t_lf2, tl.n2[gt], tl.m2);
-                const double kh = rint(sp.K * 2048.0) / 2048.0;
-                GenPair q;
-                q.Khi = (float)kh;
-                q.Klo = (float)(sp.K - kh);
-                q.pc = (float)sp.pc;
-                q.ps = (float)sp.ps;
-                q.sg = (float)sp.sg;
-                q.zero_c = sp.pc > 0;
-                q.zero_s = sp.ps > 0;
-                gp[gt] = q;
-            }
+            if (gt < NP) gp[gt] = make_seed_pair(t_lf2, tl.n2[gt], tl.m2);
             named_sync(1 + grp, 64);
             const bool valid = tl.valid[p];
             const int rp = valid ? (tl.mu2[p] - tl.j0) / 2 : nmma;   // first row of my pair
-            const GenPair q = gp[p];
+            const SeedPair q = gp[p];
             const StepCoef<float>* cp = coef + p * RMAX;
             for (int c = 0; c < NCH; ++c, ++g) {
                 const int st = g & 1;
@@ -360,19 +347,8 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
                 unsigned char* Bl = Bh + NP * OPB;
                 const int k = c * KC + kk;
                 // seed
-                const float4 tb = t_seed[k];
-                const float Lh = fmaf(q.ps, tb.z, fmaf(q.pc, tb.x, q.Khi));     // exact
-                const float Ll = fmaf(q.ps, tb.w, fmaf(q.pc, tb.y, q.Klo));
-                const float ti = floorf(Lh);
-                int e = (int)ti;
-                const float mant = exp2f((Lh - ti) + Ll);
-                int E = 0;
-                if (e < -60) {
-                    E = (-e - 60 + 119) / 120;
-                    e += 120 * E;
-                }
-                const bool zero = (q.zero_c && k == N - 1) || (q.zero_s && k == 0);
-                float cur = zero ? 0.f : q.sg * mant * __int_as_float((e + 127) << 23);
+                int E;
+                float cur = seed_value32(q, t_seed[k], k, N, E);
                 float prev = 0.f;
                 const float2 xs = t_xs[k];
                 const bool fast = __all_sync(0xffffffffu, E == 0);

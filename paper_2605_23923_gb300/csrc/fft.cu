@@ -29,6 +29,18 @@
 
 namespace su2 {
 
+// Stage-1 plane (k, s) of function f in the workspace and the offset of element
+// (mi, ni) from it: [k][s][mi][ni] or, tile-major, [s][mi][ni/4][k][ni%4].
+template <typename Cx>
+__device__ __forceinline__ const Cx* plane_base(const Cx* ws, const BandArgs& a, int f, int k, int s, int N) {
+    if (a.ws_tile_major) return ws + a.ws_off[f] + (size_t)s * N * N * N + (size_t)4 * k;
+    return ws + a.ws_off[f] + ((size_t)k * 2 + s) * N * N;
+}
+__device__ __forceinline__ size_t plane_index(const BandArgs& a, int mi, int ni, int N) {
+    if (a.ws_tile_major) return (size_t)mi * N * N + (size_t)(ni >> 2) * 4 * N + (ni & 3);
+    return (size_t)mi * N + ni;
+}
+
 template <typename T> __device__ __forceinline__ cplx<T> om_at(const BandArgs& a, int t);
 template <> __device__ __forceinline__ float2 om_at<float>(const BandArgs& a, int t) { return a.om32[t]; }
 template <> __device__ __forceinline__ double2 om_at<double>(const BandArgs& a, int t) { return a.om64[t]; }
@@ -577,7 +589,7 @@ fft_inv_cluster(BandArgs a, const cplx<T>* __restrict__ ws, cplx<T>* __restrict_
     Cx acc[NTB][R1];
 
     for (int s = 0; s < 2; ++s) {
-        const Cx* G = ws + a.ws_off[f] + ((size_t)k * 2 + s) * N * N;   // [mi][ni]
+        const Cx* G = plane_base(ws, a, f, k, s, N);   // [mi][ni]
         // Pass 1A: DFT over q (rows of G) for the owned columns p.
 #pragma unroll
         for (int it = 0; it < (W * R1) / THREADS; ++it) {
@@ -593,7 +605,7 @@ fft_inv_cluster(BandArgs a, const cplx<T>* __restrict__ ws, cplx<T>* __restrict_
                 T sg = ((ni + mi) & 1) ? T(-1) : T(1);
                 if (s) sg = -sg;
                 v[b] = (s == 0 && (ni == 0 || mi == 0)) ? mk<T>(T(0), T(0))
-                                                        : cscale(G[(size_t)mi * N + ni], sg);
+                                                        : cscale(G[plane_index(a, mi, ni, N)], sg);
             }
             dft_reg<R2, -1, T>(v);
 #pragma unroll
@@ -737,7 +749,7 @@ fft_inv_small(BandArgs a, const cplx<T>* __restrict__ ws, cplx<T>* __restrict__ 
     // each thread owns output elements e = tid (N*N <= 256)
     acc2[0] = mk<T>(T(0), T(0));
     for (int s = 0; s < 2; ++s) {
-        const Cx* G = ws + a.ws_off[f] + ((size_t)k * 2 + s) * N * N;
+        const Cx* G = plane_base(ws, a, f, k, s, N);
         __syncthreads();
         for (int e = tid; e < nE; e += blockDim.x) {      // x[q][p] = signed G
             const int q = e / N, p = e % N;
@@ -745,7 +757,7 @@ fft_inv_small(BandArgs a, const cplx<T>* __restrict__ ws, cplx<T>* __restrict__ 
             T sg = ((ni + mi) & 1) ? T(-1) : T(1);
             if (s) sg = -sg;
             x[e] = (s == 0 && (ni == 0 || mi == 0)) ? mk<T>(T(0), T(0))
-                                                    : cscale(G[(size_t)mi * N + ni], sg);
+                                                    : cscale(G[plane_index(a, mi, ni, N)], sg);
         }
         __syncthreads();
         for (int e = tid; e < nE; e += blockDim.x) {      // y[j2][p] = sum_q x[q][p] om^{q j2}

@@ -81,6 +81,48 @@ __device__ __forceinline__ double seed_log2(const BandArgs& a, int n2, int m2, i
     return L;
 }
 
+// The seed in FP32 for the complex64 paths.  Per pair, K is split as
+// K_hi + K_lo with K_hi on the 2^-11 grid; per node the table holds the same
+// split of log2 cos(beta_k/2) and log2 sin(beta_k/2) (BandArgs::seed32).  For
+// pc, ps < 2^8 every product pc * hi and the sum of the hi terms are exact in
+// FP32, so log2 |d| = L_hi + L_lo is carried to ~1e-8 absolute; then
+// |d| = 2^frac * 2^e with e an integer, stored as cur * 2^(-120 E) with the
+// scaled exponent in [-60, 60).
+struct SeedPair {
+    float Khi, Klo, pc, ps, sg;
+    int zero_c, zero_s, pad;
+};
+
+__device__ __forceinline__ SeedPair make_seed_pair(const double* lf2, int n2, int m2) {
+    const SeedParams sp = seed_params(lf2, n2, m2);
+    const double kh = rint(sp.K * 2048.0) / 2048.0;
+    SeedPair q;
+    q.Khi = (float)kh;
+    q.Klo = (float)(sp.K - kh);
+    q.pc = (float)sp.pc;
+    q.ps = (float)sp.ps;
+    q.sg = (float)sp.sg;
+    q.zero_c = sp.pc > 0;             // cos(beta/2) = 0 at the last node
+    q.zero_s = sp.ps > 0;             // sin(beta/2) = 0 at the first node
+    q.pad = 0;
+    return q;
+}
+
+__device__ __forceinline__ float seed_value32(const SeedPair& q, float4 tb, int k, int N, int& E) {
+    const float Lh = fmaf(q.ps, tb.z, fmaf(q.pc, tb.x, q.Khi));     // exact
+    const float Ll = fmaf(q.ps, tb.w, fmaf(q.pc, tb.y, q.Klo));
+    const float ti = floorf(Lh);
+    int e = (int)ti;
+    const float mant = exp2f((Lh - ti) + Ll);
+    E = 0;
+    if (e < -60) {
+        E = (-e - 60 + 119) / 120;
+        e += 120 * E;
+    }
+    const bool zero = (q.zero_c && k == N - 1) || (q.zero_s && k == 0);
+    return zero ? 0.f : q.sg * mant * __int_as_float((e + 127) << 23);
+}
+
 // Recurrence state for one (pair, node).
 template <typename T> struct Rec;
 
@@ -102,7 +144,20 @@ template <> struct Rec<float> {
         cur = (float)sg * ldexpf(mant, (int)ti);
         E = e;
     }
+    __device__ __forceinline__ void seed32(const SeedPair& q, float4 tb, float2 xs, int k, int N) {
+        cur = seed_value32(q, tb, k, N, E);
+        prev = 0.f;
+        xh = xs.x;
+        xl = xs.y;
+    }
     __device__ __forceinline__ float value() const { return E == 0 ? cur : 0.f; }
+    // plain step, for a state known to have E = 0
+    __device__ __forceinline__ void step_fast(const StepCoef<float>& c) {
+        const float xb = (xh - c.bh) + (xl - c.bl);
+        const float nxt = fmaf(c.A * xb, cur, -c.C * prev);
+        prev = cur;
+        cur = nxt;
+    }
     __device__ __forceinline__ void step(const StepCoef<float>& c) {
         const float xb = (xh - c.bh) + (xl - c.bl);
         float nxt = fmaf(c.A * xb, cur, -c.C * prev);
