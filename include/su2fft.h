@@ -111,6 +111,9 @@ su2_status su2_plan(su2_plan_t* out, const su2_plan_desc* desc);
  * (a ring of intermediate planes and its counters; tens of MB per bandwidth).
  * The content is undefined between calls and needs no initialisation. */
 su2_status su2_workspace_size(su2_plan_t plan, size_t* bytes);
+/* (The environment variable SU2_STAGE1_MAX_CTAS, if set to n >= 1, caps the
+ * grid of that forward 2-D DFT at n thread blocks; it exists to check that the
+ * kernel completes with any number of resident blocks.  Results do not change.) */
 
 /* Element offset of function f's stage-1 planes in the workspace.  Plane
  * (k, s) of f (beta node k; s = 0: integer l, s = 1: half-integer l) starts at

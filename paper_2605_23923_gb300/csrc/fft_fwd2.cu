@@ -15,12 +15,13 @@
 // The intermediate lives in a ring of plane slots at the end of the workspace;
 // a B item discards the L2 lines it has read (discard.global.L2), so a slot's
 // data normally never reaches DRAM.  Items are numbered in blocks: block t
-// holds the A items of plane t followed by the B items of plane t - D, and item
-// i belongs to CTA i mod G (all CTAs resident).  Ordering is carried by two
-// counters per ring slot: a B item waits until all A items of its plane are
-// done, and an A item reusing a slot waits until the B items of the previous
-// plane in that slot have read it.  Every wait is for an item with a smaller
-// number, so the persistent grid cannot deadlock; every wait is also bounded
+// holds the A items of plane t followed by the B items of plane t - D, and the
+// CTAs take item numbers in order from a counter in the scratch.  Ordering is
+// carried by two counters per ring slot: a B item waits until all A items of
+// its plane are done, and an A item reusing a slot waits until the B items of
+// the previous plane in that slot have read it.  Every wait is for an item with
+// a smaller number, which some running CTA already holds, so the kernel makes
+// progress whatever number of its CTAs is resident; every wait is also bounded
 // (it latches the error word and gives up).
 //
 // CTA layout: warps 0 .. CT/32-1 compute, one producer warp issues the loads
@@ -28,6 +29,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include "common.cuh"
@@ -48,7 +50,7 @@ struct Cfg {
     static constexpr int NS = 2;                        // ring slots
     static constexpr int BOXR = N < 256 ? N : 256;      // rows per TMA box (at most 256)
     static constexpr size_t smem_bytes() {
-        return (size_t)(NS + 1) * SLOT * 8 + (size_t)N * 8 * 2 + (size_t)N * 4 + 4 * 8;
+        return (size_t)(NS + 1) * SLOT * 8 + (size_t)N * 8 * 2 + (size_t)N * 4 + 2 * NS * 8 + NS * 4;
     }
     static constexpr int BLOCKS_PER_SM = (N <= 64) ? 4 : (N <= 128) ? 3 : (N <= 256 ? 2 : 1);
 };
@@ -141,6 +143,7 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
     float* wk = reinterpret_cast<float*>(tw + N);
     uint64_t* full = reinterpret_cast<uint64_t*>(wk + N);      // [NS]
     uint64_t* empty = full + NS;                               // [NS]
+    int* slot_item = reinterpret_cast<int*>(empty + NS);       // [NS] item held by a slot (-1: end)
 
     const int tid = threadIdx.x;
     const int nplanes = a.nfunc * N;
@@ -148,6 +151,7 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
     float2* ring = ws + a.ws_aux_off;                          // [RING][2][N][N]
     unsigned* doneA = reinterpret_cast<unsigned*>(ring + (size_t)RING * 2 * N * N);
     unsigned* doneB = doneA + RING;
+    unsigned* queue = doneB + RING;                            // next item number to hand out
 
     for (int t = tid; t < N; t += blockDim.x) {
         om[t] = a.om32[t];
@@ -168,13 +172,30 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
         const int lane = tid - CT;
         const uint64_t pol = policy_evict_first();
         int n = 0;
-        for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
-            const Item it = decode<N>(i, nplanes, D);
-            if (!it.valid) continue;
+        for (;;) {
+            // Items are handed out in number order, so every item this CTA waits
+            // on below is already held by a running CTA (no residency assumption).
+            int i = 0;
+            if (lane == 0) {
+                do {
+                    i = (int)atomicAdd(queue, 1u);
+                } while (i < nitems && !decode<N>(i, nplanes, D).valid);
+            }
+            i = __shfl_sync(0xffffffffu, i, 0);
             const int b = n % NS;
             const unsigned u = (unsigned)(n / NS);
             ++n;
-            if (u > 0) mbar_wait_bounded(&empty[b], (u - 1) & 1, a.err);
+            if (u > 0 && !mbar_wait_bounded(&empty[b], (u - 1) & 1, a.err)) i = nitems;
+            if (i >= nitems) {
+                if (lane == 0) {
+                    slot_item[b] = -1;
+                    mbar_arrive_cta(&full[b]);
+                }
+                break;
+            }
+            const Item it = decode<N>(i, nplanes, D);
+            if (lane == 0) slot_item[b] = i;          // published by the arrive on full[b]
+            __syncwarp();
             const int r = it.plane % RING;
             const unsigned use = (unsigned)(it.plane / RING);
             float2* dst = S + b * SLOT;
@@ -210,16 +231,17 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
     // ----------------------------------------------------------------- compute
     const int warp = tid >> 5, lane = tid & 31;
     int n = 0;
-    for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
-        const Item it = decode<N>(i, nplanes, D);
-        if (!it.valid) continue;
+    for (;;) {
         const int b = n % NS;
         const unsigned u = (unsigned)(n / NS);
         ++n;
+        if (!mbar_wait_bounded(&full[b], u & 1, a.err)) break;
+        const int i = slot_item[b];
+        if (i < 0) break;
+        const Item it = decode<N>(i, nplanes, D);
         float2* X = S + b * SLOT;
         const int r = it.plane % RING;
         const int fb = it.plane / N, k = it.plane % N;
-        mbar_wait_bounded(&full[b], u & 1, a.err);
 
         if (it.isA) {
             // Pass a: R2-point DFTs over j1 = ia + R1*b (stride R1), both sectors.
@@ -370,7 +392,7 @@ static cudaError_t launch_n(const BandArgs& a, const void* in, void* out, cudaSt
     if (RING != a.aux_ring) return cudaErrorInvalidValue;          // plan built for another device shape
     float2* ring = (float2*)out + a.ws_aux_off;
     unsigned* ctr = reinterpret_cast<unsigned*>(ring + (size_t)RING * 2 * N * N);
-    if ((e = cudaMemsetAsync(ctr, 0, sizeof(unsigned) * 2 * RING, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ctr, 0, sizeof(unsigned) * (2 * RING + 1), st)) != cudaSuccess) return e;
     CUtensorMap gmap;
     memset(&gmap, 0, sizeof(gmap));
     BandArgs b = a;
@@ -382,7 +404,13 @@ static cudaError_t launch_n(const BandArgs& a, const void* in, void* out, cudaSt
         if (!encode_tensor_map_8b(&gmap, 3, base, dims, strides, box)) b.grid_regular = 0;
     }
     const int nitems = (a.nfunc * N + D) * P::IB;
-    const int grid = G < nitems ? G : nitems;
+    int grid = G < nitems ? G : nitems;
+    // SU2_STAGE1_MAX_CTAS caps the grid (robustness checks: the in-order queue
+    // must finish with any number of resident CTAs, down to one)
+    if (const char* cap = getenv("SU2_STAGE1_MAX_CTAS")) {
+        const int c = atoi(cap);
+        if (c >= 1 && c < grid) grid = c;
+    }
     const int discard_ok = ((uintptr_t)ring % 128) == 0;
     fft_fwd_two_phase<N><<<grid, P::THREADS, P::smem_bytes(), st>>>(b, gmap, (const float2*)in, (float2*)out, D,
                                                                    RING, discard_ok);
@@ -405,9 +433,9 @@ cudaError_t fft_forward_aux(int N, int device, int* ring, size_t* elems) {
     }
     if (e != cudaSuccess) return e;
     *ring = R;
-    // ring planes (2 N^2 complex each) + 2 R counters, rounded up to 256 bytes so
+    // ring planes (2 N^2 complex each) + 2 R counters + the item queue, rounded up to 256 bytes so
     // that the next bandwidth's ring starts on a 128-byte L2 line as well
-    *elems = (size_t)R * 2 * N * N + ((size_t)2 * R * sizeof(unsigned) + 255) / 256 * 32;
+    *elems = (size_t)R * 2 * N * N + ((size_t)(2 * R + 1) * sizeof(unsigned) + 255) / 256 * 32;
     return cudaSuccess;
 }
 

@@ -136,3 +136,35 @@ def test_stage1_planes_tensor_core_layout(su2, N, B):
     plan.sync_status()
     for fi, g in enumerate(grids):
         check_planes(plan, ws, g.astype(np.complex128), fi, [0, 1, N // 2, N - 1], tile_major=True)
+
+
+def test_stage1_two_phase_with_few_resident_blocks(su2):
+    """The two-phase DFT hands out items in order, so it completes with any
+    number of resident thread blocks; the grid is capped at 1 and 5 blocks (in a
+    child process, the cap being read from the environment at launch)."""
+    import os
+    import subprocess
+    import sys
+    code = r'''
+import numpy as np, torch, sys
+sys.path.insert(0, ".")
+import su2inputs as I
+import paper_2605_23923_gb300 as su2
+from tests.test_gpu_stage1 import check_planes
+N, B = 128, 2
+rng = np.random.default_rng(51)
+grids = [I.draw_grid_gaussian((N, N, N), rng).astype(np.complex64) for _ in range(B)]
+plan = su2.Plan(N=N, batch=B, dtype="c64")
+x = torch.from_numpy(np.concatenate([g.reshape(-1) for g in grids])).cuda()
+ws = plan.forward_stage1(x)
+plan.sync_status()
+for fi, g in enumerate(grids):
+    check_planes(plan, ws, g.astype(np.complex128), fi, [0, 9, N // 2, N - 1])
+print("ok")
+'''
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for cap in ("1", "5"):
+        env = dict(os.environ, SU2_STAGE1_MAX_CTAS=cap)
+        r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True,
+                           timeout=600)
+        assert r.returncode == 0 and r.stdout.strip().endswith("ok"), (cap, r.stdout[-2000:], r.stderr[-2000:])
