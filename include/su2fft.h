@@ -78,7 +78,9 @@ typedef enum {
     SU2_ALGO_FP64 = 1,         /* c128 only: FP64 DFT, FP64 recurrence/contraction */
     SU2_ALGO_FP32 = 2,         /* c64: FP32 DFT, FP32 recurrence, FP32 FMA contraction */
     SU2_ALGO_TC_BF16X3 = 3     /* c64: FP32 DFT, contraction on tensor cores with
-                                  split-BF16 operands (3 products), FP32 accumulate */
+                                  split-BF16 operands (3 products), FP32 accumulate,
+                                  for N = 64, 128, 256; functions of other
+                                  bandwidths in the plan take the FP32 path */
 } su2_algo;
 
 typedef enum {
@@ -93,9 +95,23 @@ typedef struct {
     su2_dtype dtype;
     su2_algo algo;
     su2_weights weights;
-    unsigned flags;      /* reserved, must be 0                                   */
+    unsigned flags;      /* SU2_FLAG_* bits below, others must be 0               */
     int device;          /* CUDA device ordinal the plan's tables live on        */
 } su2_plan_desc;
+
+/* Plan flags (library services; the paper has no counterpart).
+ * SU2_FLAG_CUDA_GRAPH: su2_forward records the whole forward transform (every
+ *   bandwidth group, groups running concurrently) once per (grid, coeffs, ws)
+ *   pointer triple into a CUDA graph owned by the plan and afterwards replays
+ *   it with one graph launch on the caller's stream.  The plan keeps the 8
+ *   most recent graphs.  The first call with new pointers must not itself be
+ *   made during a stream capture.
+ * SU2_FLAG_AUTOTUNE: su2_plan times the candidate kernels of every complex64
+ *   bandwidth group (forward 2-D DFT variant at N = 64, 128; functions per
+ *   block of the FP32 contraction) on scratch buffers it allocates and frees,
+ *   and keeps the fastest.  Results do not depend on the choice. */
+#define SU2_FLAG_CUDA_GRAPH 0x1u
+#define SU2_FLAG_AUTOTUNE 0x2u
 
 /* Supported bandwidths: N a power of two with 4 <= N <= 512 (c64) and
  * 4 <= N <= 256 (c128).  Anything else returns SU2_ERR_UNSUPPORTED. */
@@ -127,7 +143,10 @@ su2_status su2_workspace_size(su2_plan_t plan, size_t* bytes);
  * nodes contiguous, the operand tiles of the tensor-core contraction). */
 su2_status su2_plane_offset(su2_plan_t plan, int f, size_t* elems);
 
-/* Element offsets of function f inside the grid and coefficient buffers. */
+/* Element offsets of function f inside the grid and coefficient buffers.
+ * Grids are grouped by bandwidth (increasing N; batch order inside a group), so
+ * each group is one regularly strided array; coefficients follow batch order.
+ * For a uniform batch both are simply f * N^3 and f * su2_num_coeffs(N). */
 su2_status su2_grid_offset(su2_plan_t plan, int f, size_t* elems);
 su2_status su2_coeff_offset(su2_plan_t plan, int f, size_t* elems);
 /* Total elements of the grid and coefficient buffers for the whole batch. */

@@ -40,7 +40,8 @@ class Plan:
     """A transform plan for a batch of functions (uniform or ragged bandwidths)."""
 
     def __init__(self, N=None, batch: int = 1, dtype: str = "c64", algo: str = "auto",
-                 weights: str = "cc", device: int | None = None, Ns=None):
+                 weights: str = "cc", device: int | None = None, Ns=None, graph: bool = False,
+                 autotune: bool = False):
         self._lib = load()
         if Ns is not None:
             Ns = [int(n) for n in Ns]
@@ -63,7 +64,7 @@ class Plan:
         desc.dtype = _abi.DTYPES[dtype]
         desc.algo = _abi.ALGOS[algo]
         desc.weights = _abi.WEIGHTS[weights]
-        desc.flags = 0
+        desc.flags = (_abi.FLAG_CUDA_GRAPH if graph else 0) | (_abi.FLAG_AUTOTUNE if autotune else 0)
         desc.device = self.device
         h = ctypes.c_void_p()
         _abi.check("su2_plan", self._lib.su2_plan(ctypes.byref(h), ctypes.byref(desc)))

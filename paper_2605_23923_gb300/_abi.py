@@ -43,6 +43,9 @@ class SU2Error(RuntimeError):
 _lib = None
 
 # (name, restype, argtypes) for every entry point of include/su2fft.h
+FLAG_CUDA_GRAPH = 0x1
+FLAG_AUTOTUNE = 0x2
+
 SIGNATURES = [
     ("su2_plan", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(PlanDesc)]),
     ("su2_workspace_size", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),

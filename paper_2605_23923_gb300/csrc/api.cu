@@ -15,6 +15,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <map>
 #include <new>
@@ -42,6 +43,9 @@ struct Band {
     double2* d_twist64 = nullptr;
     size_t aux_off = 0;           // stage-1 scratch (two-phase DFT ring) in the workspace
     int aux_ring = 0;
+    bool tc = false;              // contraction on tensor cores (tile-major planes)
+    int s1_two_phase = 0;         // kernel choices (defaults, or the autotuner's)
+    int s2_bt = 0;
 };
 
 struct DeviceGuard {
@@ -97,6 +101,19 @@ struct su2_plan_s {
     size_t* d_ws_off = nullptr;
     double* d_lf2 = nullptr;
     int* d_err = nullptr;
+    unsigned flags = 0;
+    // concurrent bandwidth groups: one stream per group, fork/join events
+    std::vector<cudaStream_t> band_streams;
+    std::vector<cudaEvent_t> ev_join;
+    cudaEvent_t ev_fork = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    struct GraphEntry {
+        const void* grid;
+        void* coeffs;
+        void* ws;
+        cudaGraphExec_t exec;
+    };
+    std::vector<GraphEntry> graphs;   // most recent last
 
     template <typename T>
     cudaError_t upload(T** dst, const T* src, size_t count) {
@@ -108,6 +125,16 @@ struct su2_plan_s {
         return cudaMemcpy(p, src, count * sizeof(T), cudaMemcpyHostToDevice);
     }
     void release() {
+        for (auto& ge : graphs) cudaGraphExecDestroy(ge.exec);
+        graphs.clear();
+        for (cudaStream_t s : band_streams) cudaStreamDestroy(s);
+        band_streams.clear();
+        for (cudaEvent_t ev : ev_join) cudaEventDestroy(ev);
+        ev_join.clear();
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        ev_fork = nullptr;
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+        cap_stream = nullptr;
         for (void* p : allocs) cudaFree(p);
         allocs.clear();
     }
@@ -208,11 +235,181 @@ su2::BandArgs band_args(const su2_plan_s* P, const Band& b) {
     a.grid_regular = 1;
     a.ws_aux_off = b.aux_off;
     a.aux_ring = b.aux_ring;
-    a.ws_tile_major = (P->algo == SU2_ALGO_TC_BF16X3) ? 1 : 0;
+    a.ws_tile_major = b.tc ? 1 : 0;
+    a.s1_two_phase = b.s1_two_phase;
+    a.s2_bt = b.s2_bt;
     const size_t n3 = (size_t)b.N * b.N * b.N;
     for (size_t i = 0; i < b.fids.size(); ++i)
         if (P->grid_off[b.fids[i]] != a.grid_group_off + i * n3) a.grid_regular = 0;
     return a;
+}
+
+// Forward transform of one bandwidth group on one stream.
+cudaError_t launch_band_forward(const su2_plan_s* P, const Band& b, const void* grid, void* coeffs, void* ws,
+                                cudaStream_t st) {
+    const su2::BandArgs a = band_args(P, b);
+    const bool fp64 = P->dtype == SU2_C128;
+    cudaError_t e = su2::launch_fft_forward(a, fp64, grid, ws, st);
+    if (e != cudaSuccess) return e;
+    if (b.tc) return su2::launch_contract_forward_tc(a, ws, coeffs, st);
+    return su2::launch_contract_forward(a, fp64, ws, coeffs, st);
+}
+
+// Every group's forward transform; with several groups they run concurrently
+// on the plan's streams, forked from and joined back into `st`.
+cudaError_t enqueue_forward(su2_plan_s* P, const void* grid, void* coeffs, void* ws, cudaStream_t st) {
+    if (P->band_streams.empty()) {
+        for (auto& kv : P->bands) {
+            const cudaError_t e = launch_band_forward(P, kv.second, grid, coeffs, ws, st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    cudaError_t e = cudaEventRecord(P->ev_fork, st);
+    if (e != cudaSuccess) return e;
+    size_t i = 0;
+    for (auto& kv : P->bands) {
+        cudaStream_t bs = P->band_streams[i];
+        if ((e = cudaStreamWaitEvent(bs, P->ev_fork, 0)) != cudaSuccess) return e;
+        const cudaError_t el = launch_band_forward(P, kv.second, grid, coeffs, ws, bs);
+        if ((e = cudaEventRecord(P->ev_join[i], bs)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(st, P->ev_join[i], 0)) != cudaSuccess) return e;
+        if (el != cudaSuccess) return el;
+        ++i;
+    }
+    return cudaSuccess;
+}
+
+// The forward transform as a CUDA graph recorded once per pointer triple.
+cudaError_t forward_graph(su2_plan_s* P, const void* grid, void* coeffs, void* ws, cudaStream_t st) {
+    for (size_t i = 0; i < P->graphs.size(); ++i) {
+        const auto ge = P->graphs[i];
+        if (ge.grid == grid && ge.coeffs == coeffs && ge.ws == ws) {
+            P->graphs.erase(P->graphs.begin() + (long)i);
+            P->graphs.push_back(ge);
+            return cudaGraphLaunch(ge.exec, st);
+        }
+    }
+    cudaError_t e = cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    const cudaError_t eq = enqueue_forward(P, grid, coeffs, ws, P->cap_stream);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(P->cap_stream, &graph);
+    if (eq != cudaSuccess || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return eq != cudaSuccess ? eq : e;
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return e;
+    if (P->graphs.size() >= 8) {
+        cudaGraphExecDestroy(P->graphs.front().exec);
+        P->graphs.erase(P->graphs.begin());
+    }
+    P->graphs.push_back({grid, coeffs, ws, exec});
+    return cudaGraphLaunch(exec, st);
+}
+
+// Autotuner: for each complex64 group, time the candidate kernels on scratch
+// buffers holding up to 32 of its functions and keep the fastest.
+cudaError_t time_ms(cudaStream_t st, float* ms, const std::function<cudaError_t()>& fn) {
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaEventCreate(&e1)) != cudaSuccess) { cudaEventDestroy(e0); return e; }
+    e = fn();                                            // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = fn();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return e;
+}
+
+cudaError_t autotune(su2_plan_s* P) {
+    if (P->dtype != SU2_C64) return cudaSuccess;
+    cudaStream_t st;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    for (auto& kv : P->bands) {
+        Band& b = kv.second;
+        const int N = kv.first;
+        const bool try_s1 = b.aux_ring > 0 && !b.tc && (N == 64 || N == 128);
+        const bool try_s2 = !b.tc;
+        if (!try_s1 && !try_s2) continue;
+        const int nb = std::min((int)b.fids.size(), 32);
+        const size_t n3 = (size_t)N * N * N;
+        std::vector<int> fidx(nb);
+        std::vector<size_t> goff(nb), coff(nb), woff(nb);
+        for (int i = 0; i < nb; ++i) {
+            fidx[i] = i;
+            goff[i] = (size_t)i * n3;
+            coff[i] = (size_t)i * ncoef(N);
+            woff[i] = (size_t)i * 2 * n3;
+        }
+        const size_t aux = b.aux_ring > 0 ? (b.aux_ring * 2 * (size_t)N * N + 64 * 32) : 0;
+        void *dg = nullptr, *dw = nullptr, *dc = nullptr, *dt = nullptr;
+        const size_t tbytes = nb * sizeof(int) + 3 * nb * sizeof(size_t);
+        e = cudaMalloc(&dg, nb * n3 * 8);
+        if (e == cudaSuccess) e = cudaMalloc(&dw, (nb * 2 * n3 + aux) * 8);
+        if (e == cudaSuccess) e = cudaMalloc(&dc, nb * ncoef(N) * 8);
+        if (e == cudaSuccess) e = cudaMalloc(&dt, tbytes);
+        if (e == cudaSuccess) e = cudaMemsetAsync(dg, 0, nb * n3 * 8, st);
+        size_t* dgo = reinterpret_cast<size_t*>(dt);
+        size_t* dco = dgo + nb;
+        size_t* dwo = dco + nb;
+        int* dfi = reinterpret_cast<int*>(dwo + nb);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dgo, goff.data(), nb * sizeof(size_t), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dco, coff.data(), nb * sizeof(size_t), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dwo, woff.data(), nb * sizeof(size_t), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dfi, fidx.data(), nb * sizeof(int), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        su2::BandArgs t = band_args(P, b);
+        t.nfunc = nb;
+        t.fidx = dfi;
+        t.grid_off = dgo;
+        t.coeff_off = dco;
+        t.ws_off = dwo;
+        t.ws_group_off = 0;
+        t.grid_group_off = 0;
+        t.grid_regular = 1;
+        t.ws_aux_off = (size_t)nb * 2 * n3;
+        if (e == cudaSuccess && try_s1) {
+            float best = 1e30f;
+            int pick = b.s1_two_phase;
+            for (int cand = 0; cand < 2 && e == cudaSuccess; ++cand) {
+                t.s1_two_phase = cand;
+                float ms = 0.f;
+                e = time_ms(st, &ms, [&]() { return su2::launch_fft_forward(t, false, dg, dw, st); });
+                if (e == cudaSuccess && ms < best) { best = ms; pick = cand; }
+            }
+            b.s1_two_phase = pick;
+            t.s1_two_phase = pick;
+        }
+        if (e == cudaSuccess && try_s2) {
+            float best = 1e30f;
+            int pick = 0;
+            for (int cand : {8, 16}) {
+                if (e != cudaSuccess) break;
+                t.s2_bt = cand;
+                float ms = 0.f;
+                e = time_ms(st, &ms, [&]() { return su2::launch_contract_forward(t, false, dw, dc, st); });
+                if (e == cudaSuccess && ms < best) { best = ms; pick = cand; }
+            }
+            b.s2_bt = pick;
+        }
+        cudaStreamSynchronize(st);
+        if (dg) cudaFree(dg);
+        if (dw) cudaFree(dw);
+        if (dc) cudaFree(dc);
+        if (dt) cudaFree(dt);
+        if (e != cudaSuccess) break;
+    }
+    cudaStreamDestroy(st);
+    return e;
 }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
@@ -250,7 +447,8 @@ const char* su2_status_string(su2_status s) {
 
 su2_status su2_plan(su2_plan_t* out, const su2_plan_desc* desc) {
     if (!out || !desc) return SU2_ERR_INVALID_ARG;
-    if (desc->num_functions < 1 || desc->flags != 0) return SU2_ERR_INVALID_ARG;
+    if (desc->num_functions < 1 || (desc->flags & ~(SU2_FLAG_CUDA_GRAPH | SU2_FLAG_AUTOTUNE)) != 0)
+        return SU2_ERR_INVALID_ARG;
     if (desc->dtype != SU2_C64 && desc->dtype != SU2_C128) return SU2_ERR_INVALID_ARG;
     if (desc->weights != SU2_WEIGHTS_CC && desc->weights != SU2_WEIGHTS_RIEMANN) return SU2_ERR_INVALID_ARG;
     su2_algo algo = desc->algo;
@@ -262,7 +460,6 @@ su2_status su2_plan(su2_plan_t* out, const su2_plan_desc* desc) {
     for (int f = 0; f < desc->num_functions; ++f) {
         const int N = desc->N ? desc->N[f] : desc->N_uniform;
         if (!is_pow2(N) || N < 4 || N > Nmax_allowed) return SU2_ERR_UNSUPPORTED;
-        if (algo == SU2_ALGO_TC_BF16X3 && !su2::tc_supported(N)) return SU2_ERR_UNSUPPORTED;
         Ns[f] = N;
     }
     int ndev = 0;
@@ -278,6 +475,7 @@ su2_status su2_plan(su2_plan_t* out, const su2_plan_desc* desc) {
     P->dtype = desc->dtype;
     P->algo = algo;
     P->weights = desc->weights;
+    P->flags = desc->flags;
     P->Ns = Ns;
     P->grid_off.resize(P->B);
     P->coeff_off.resize(P->B);
@@ -285,12 +483,18 @@ su2_status su2_plan(su2_plan_t* out, const su2_plan_desc* desc) {
     int Nmax = 0;
     for (int f = 0; f < P->B; ++f) {
         const size_t N = (size_t)Ns[f];
-        P->grid_off[f] = P->grid_total;
         P->coeff_off[f] = P->coeff_total;
-        P->grid_total += N * N * N;
         P->coeff_total += ncoef((int)N);
         P->bands[(int)N].fids.push_back(f);
         Nmax = std::max(Nmax, (int)N);
+    }
+    // grids: contiguous per bandwidth group (bands in increasing N, batch order inside)
+    for (auto& kv : P->bands) {
+        const size_t N = (size_t)kv.first;
+        for (int f : kv.second.fids) {
+            P->grid_off[f] = P->grid_total;
+            P->grid_total += N * N * N;
+        }
     }
     // stage-1 planes: contiguous per bandwidth group, functions in batch order,
     // so that a group's planes form one regularly strided array
@@ -303,9 +507,10 @@ su2_status su2_plan(su2_plan_t* out, const su2_plan_desc* desc) {
     }
     // scratch of the two-phase stage-1 DFT, after all planes
     for (auto& kv : P->bands) {
+        kv.second.tc = algo == SU2_ALGO_TC_BF16X3 && su2::tc_supported(kv.first);
         // complex64 at N >= 128; the tensor-core path also at N = 64 (its planes are tile-major)
         if (!su2::fft_forward_two_phase_supported(kv.first, desc->dtype == SU2_C128)) continue;
-        if (kv.first < 128 && algo != SU2_ALGO_TC_BF16X3) continue;
+        if (kv.first < 128 && !kv.second.tc && !(desc->flags & SU2_FLAG_AUTOTUNE)) continue;
         size_t elems = 0;
         int ring = 0;
         const cudaError_t ea = su2::fft_forward_aux(kv.first, desc->device, &ring, &elems);
@@ -315,6 +520,7 @@ su2_status su2_plan(su2_plan_t* out, const su2_plan_desc* desc) {
         }
         kv.second.aux_off = P->ws_total;
         kv.second.aux_ring = ring;
+        kv.second.s1_two_phase = (kv.first >= 128 || kv.second.tc) ? 1 : 0;
         P->ws_total += elems;
     }
     std::vector<double> lf2(2 * Nmax + 2);
@@ -332,7 +538,22 @@ su2_status su2_plan(su2_plan_t* out, const su2_plan_desc* desc) {
         if (e != cudaSuccess) break;
         kv.second.N = kv.first;
         e = build_band(P, kv.second);
+        if (kv.second.s2_bt == 0) kv.second.s2_bt = kv.second.fids.size() <= 8 ? 8 : 16;
     }
+    if (e == cudaSuccess && P->bands.size() > 1) {
+        e = cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming);
+        for (size_t i = 0; i < P->bands.size() && e == cudaSuccess; ++i) {
+            cudaStream_t bs = nullptr;
+            cudaEvent_t ev = nullptr;
+            e = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
+            if (e == cudaSuccess) P->band_streams.push_back(bs);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e == cudaSuccess) P->ev_join.push_back(ev);
+        }
+    }
+    if (e == cudaSuccess && (P->flags & SU2_FLAG_CUDA_GRAPH))
+        e = cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && (P->flags & SU2_FLAG_AUTOTUNE)) e = autotune(P);
     if (e != cudaSuccess) {
         P->release();
         delete P;
@@ -384,17 +605,9 @@ su2_status su2_forward(su2_plan_t plan, const void* grid, void* coeffs, void* ws
     DeviceGuard g(plan->device);
     if (!g.ok) return SU2_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
-    const bool fp64 = plan->dtype == SU2_C128;
-    for (auto& kv : plan->bands) {
-        const su2::BandArgs a = band_args(plan, kv.second);
-        cudaError_t e = su2::launch_fft_forward(a, fp64, grid, ws, st);
-        if (e == cudaSuccess) {
-            if (plan->algo == SU2_ALGO_TC_BF16X3) e = su2::launch_contract_forward_tc(a, ws, coeffs, st);
-            else e = su2::launch_contract_forward(a, fp64, ws, coeffs, st);
-        }
-        if (e != cudaSuccess) return from_cuda(e);
-    }
-    return SU2_OK;
+    const cudaError_t e = (plan->flags & SU2_FLAG_CUDA_GRAPH) ? forward_graph(plan, grid, coeffs, ws, st)
+                                                             : enqueue_forward(plan, grid, coeffs, ws, st);
+    return from_cuda(e);
 }
 
 su2_status su2_forward_stage1(su2_plan_t plan, const void* grid, void* ws, void* stream) {
@@ -418,7 +631,7 @@ su2_status su2_forward_stage2(su2_plan_t plan, const void* ws, void* coeffs, voi
     const bool fp64 = plan->dtype == SU2_C128;
     for (auto& kv : plan->bands) {
         const su2::BandArgs a = band_args(plan, kv.second);
-        cudaError_t e = (plan->algo == SU2_ALGO_TC_BF16X3)
+        cudaError_t e = kv.second.tc
                             ? su2::launch_contract_forward_tc(a, ws, coeffs, (cudaStream_t)stream)
                             : su2::launch_contract_forward(a, fp64, ws, coeffs, (cudaStream_t)stream);
         if (e != cudaSuccess) return from_cuda(e);

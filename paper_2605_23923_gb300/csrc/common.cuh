@@ -312,6 +312,8 @@ struct BandArgs {
     int aux_ring;                 // plane slots of that ring (0: none)
     int ws_tile_major;            // 1: stage-1 planes of a function stored [s][mi][ni/4][k][ni%4]
                                   // (tensor-core plans), 0: [k][s][mi][ni]
+    int s1_two_phase;             // forward 2-D DFT: 1 two-phase kernel (needs aux_ring > 0), 0 cluster
+    int s2_bt;                    // FP32 forward contraction: functions per block (8 or 16; 0: by batch)
 };
 
 }  // namespace su2

@@ -515,8 +515,10 @@ static cudaError_t launch_fwd_t(const BandArgs& a, const void* ws, void* coeffs,
 cudaError_t launch_contract_forward(const BandArgs& a, bool fp64, const void* ws, void* coeffs, cudaStream_t st) {
     if (a.nfunc <= 0) return cudaSuccess;
     if (fp64) return launch_fwd_t<double, 4, 8, 32, 64, 4, 2>(a, ws, coeffs, st);
-    // small batches: 8 functions per CTA, so that no FMA lane works on padding
-    if (a.nfunc <= 8) return launch_fwd_t<float, 4, 8, 16, 128, 8, 4>(a, ws, coeffs, st);
+    // 8 or 16 functions per block (chosen by the plan's autotuner, else by batch
+    // size: small batches take 8 so that no FMA lane works on padding)
+    const int bt = a.s2_bt ? a.s2_bt : (a.nfunc <= 8 ? 8 : 16);
+    if (bt == 8) return launch_fwd_t<float, 4, 8, 16, 128, 8, 4>(a, ws, coeffs, st);
     return launch_fwd_t<float, 4, 16, 32, 128, 8, 4>(a, ws, coeffs, st);
 }
 

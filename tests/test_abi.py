@@ -61,7 +61,7 @@ def test_plan_validation_on_host(lib):
     h = ctypes.c_void_p()
     assert lib.su2_plan(None, None) == 1
     assert lib.su2_plan(ctypes.byref(h), ctypes.byref(_desc(num_functions=0))) == 1
-    assert lib.su2_plan(ctypes.byref(h), ctypes.byref(_desc(flags=3))) == 1
+    assert lib.su2_plan(ctypes.byref(h), ctypes.byref(_desc(flags=0x80))) == 1
     assert lib.su2_plan(ctypes.byref(h), ctypes.byref(_desc(N=48))) == 2       # not a power of two
     assert lib.su2_plan(ctypes.byref(h), ctypes.byref(_desc(N=2))) == 2
     assert lib.su2_plan(ctypes.byref(h), ctypes.byref(_desc(N=1024))) == 2

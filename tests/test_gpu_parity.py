@@ -49,7 +49,9 @@ def run_forward(su2, grids, dtype, Ns=None, weights="cc", algo="auto"):
         plan = su2.Plan(N=grids[0].shape[0], batch=len(grids), dtype=dtype, weights=weights, algo=algo)
     else:
         plan = su2.Plan(Ns=Ns, dtype=dtype, weights=weights, algo=algo)
-    flat = np.concatenate([g.reshape(-1) for g in grids])
+    flat = np.zeros(plan.grid_elems, dtype=np.complex128)
+    for g, o in zip(grids, plan.grid_offsets):          # the plan decides where each grid goes
+        flat[o:o + g.size] = g.reshape(-1)
     out = plan.forward(to_dev(flat, dtype))
     plan.sync_status()
     out = out.cpu().numpy().astype(np.complex128)
@@ -291,3 +293,24 @@ def test_full_size_n256_b64_sampled(su2, algo):
                 worst = max(worst, abs(got[G.coeff_index(j0 + 2 * i, m2, n2)] - v))
                 scale = max(scale, abs(v))
         assert worst / scale < TOL32, (b, worst / scale)
+
+
+def test_forward_tc_mixed_bandwidths(su2):
+    """A tensor-core plan with bandwidths outside {64, 128, 256}: those groups
+    take the FP32 contraction, the others the tensor cores."""
+    Ns = [16, 64, 32, 128, 16]
+    rng = np.random.default_rng(13)
+    grids = [cast(I.draw_grid_gaussian((n, n, n), rng), "c64") for n in Ns]
+    _, outs = run_forward(su2, grids, "c64", Ns=Ns, algo="tc_bf16x3")
+    from oracle import grid as G
+    for n, g, o in zip(Ns, grids, outs):
+        if n <= 64:
+            assert rel(o, T.forward_separable(g)) < TOL32, n
+        else:
+            worst = scale = 0.0
+            for n2, m2 in [(0, 0), (126, -126), (127, 127), (-5, 3), (44, 44), (-1, -127)]:
+                j0, vals = T.forward_pair(g, n2, m2)
+                for i, v in enumerate(vals):
+                    worst = max(worst, abs(o[G.coeff_index(j0 + 2 * i, m2, n2)] - v))
+                    scale = max(scale, abs(v))
+            assert worst / scale < TOL32

@@ -86,7 +86,10 @@ def test_stage1_planes_ragged(su2):
     rng = np.random.default_rng(47)
     grids = [I.draw_grid_gaussian((n, n, n), rng).astype(np.complex64) for n in Ns]
     plan = su2.Plan(Ns=Ns, dtype="c64")
-    x = torch.from_numpy(np.concatenate([g.reshape(-1) for g in grids])).cuda()
+    flat = np.zeros(plan.grid_elems, dtype=np.complex64)
+    for g, o in zip(grids, plan.grid_offsets):          # grids are grouped by bandwidth
+        flat[o:o + g.size] = g.reshape(-1)
+    x = torch.from_numpy(flat).cuda()
     ws = plan.forward_stage1(x)
     plan.sync_status()
     for fi, (n, g) in enumerate(zip(Ns, grids)):
