@@ -32,6 +32,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "su2_internal.h"
 
@@ -46,11 +48,13 @@ struct Cfg {
     static constexpr int NA = NH, NB = 2 * NH, IB = NA + NB;
     static constexpr int CT = W * (R1 > R2 ? R1 : R2);  // compute threads
     static constexpr int THREADS = CT + 32;
-    static constexpr int SLOT = W * N;                  // float2 per ring slot
+    static constexpr int SLOT = W * N;                  // float2 of an A slab / B block
+    static constexpr int PB = N + 1;                    // row pitch of a B block in the slot
+    static constexpr int SLOTP = SLOT + 16;             // slot stride (B pitch padding; 128-B multiple)
     static constexpr int NS = 2;                        // ring slots
     static constexpr int BOXR = N < 256 ? N : 256;      // rows per TMA box (at most 256)
     static constexpr size_t smem_bytes() {
-        return (size_t)(NS + 1) * SLOT * 8 + (size_t)N * 8 * 2 + (size_t)N * 4 + 2 * NS * 8 + NS * 4;
+        return (size_t)(NS + 1) * SLOTP * 8 + (size_t)N * 8 * 2 + (size_t)N * 4 + 2 * NS * 8 + NS * 4;
     }
     static constexpr int BLOCKS_PER_SM = (N <= 64) ? 4 : (N <= 128) ? 3 : (N <= 256 ? 2 : 1);
 };
@@ -137,8 +141,8 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
     constexpr int R1 = P::R1, R2 = P::R2, W = P::W, CT = P::CT, SLOT = P::SLOT, NS = P::NS;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float2* S = reinterpret_cast<float2*>(smem_raw);          // [NS][SLOT] ring
-    float2* Y = S + NS * SLOT;                                 // sector-1 columns of an A item
-    float2* om = Y + SLOT;                                     // exp(+2 pi i t/N)
+    float2* Y = S + NS * P::SLOTP;                             // sector-1 columns of an A item
+    float2* om = Y + P::SLOTP;                                 // exp(+2 pi i t/N)
     float2* tw = om + N;                                       // exp(+i pi t/N)
     float* wk = reinterpret_cast<float*>(tw + N);
     uint64_t* full = reinterpret_cast<uint64_t*>(wk + N);      // [NS]
@@ -198,7 +202,7 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
             __syncwarp();
             const int r = it.plane % RING;
             const unsigned use = (unsigned)(it.plane / RING);
-            float2* dst = S + b * SLOT;
+            float2* dst = S + b * P::SLOTP;
             if (it.isA) {
                 const int fb = it.plane / N, k = it.plane % N;
                 if (lane == 0 && use > 0) wait_counter(&doneB[r], use * P::NB, a.err);
@@ -239,7 +243,7 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
         const int i = slot_item[b];
         if (i < 0) break;
         const Item it = decode<N>(i, nplanes, D);
-        float2* X = S + b * SLOT;
+        float2* X = S + b * P::SLOTP;
         const int r = it.plane % RING;
         const int fb = it.plane / N, k = it.plane % N;
 
@@ -290,7 +294,7 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
             }
         } else {
             // Pass a: R2-point DFTs over j2 = ia + R1*q of row pl, read straight from
-            // the intermediate in L2; written back XOR-swizzled into the slot.
+            // the intermediate in L2; written into the slot with the odd row pitch N + 1.
             const float2* rows = ring + ((size_t)(r * 2 + it.s) * N + it.pb * W) * N;
             {
                 const int ia = tid % R1, pl = tid / R1;            // W * R1 == CT
@@ -306,7 +310,7 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
                 for (int q = 1; q < R2; ++q) v[q] = cmul(v[q], om[ia * q]);
                 named_sync(1, CT);        // every load of the item has been consumed
 #pragma unroll
-                for (int q = 0; q < R2; ++q) X[pl * N + ((ia + R1 * q) ^ (pl & 15))] = v[q];
+                for (int q = 0; q < R2; ++q) X[pl * P::PB + ia + R1 * q] = v[q];   // odd pitch: no conflicts
                 fence_proxy_async_smem();   // before the slot is refilled by TMA
             }
             // The rows are in registers / shared memory: drop them from L2, release them.
@@ -324,7 +328,7 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
                 const int pl = tid % W, qb = tid / W;
                 float2 v[R1];
 #pragma unroll
-                for (int ia = 0; ia < R1; ++ia) v[ia] = X[pl * N + ((ia + R1 * qb) ^ (pl & 15))];
+                for (int ia = 0; ia < R1; ++ia) v[ia] = X[pl * P::PB + ia + R1 * qb];
                 named_sync(2, W * R2);
                 if (lane == 0) mbar_arrive_cta(&empty[b]);
                 dft_reg<R1, 1, float>(v);
@@ -334,28 +338,33 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
                 const int p = it.pb * W + pl;
                 const int ni = (p + N / 2) & (N - 1);
                 // element (mi) of this thread's column ni: [k][s][mi][ni] or, tile-major,
-                // [s][mi][ni/4][k][ni%4] (4 consecutive n of 256 nodes contiguous)
-                float2* out;
-                size_t mstride;
-                if (a.ws_tile_major) {
-                    out = ws + plane_off + (size_t)it.s * N * N * N + (size_t)(ni >> 2) * N * 4 + (size_t)k * 4 + (ni & 3);
-                    mstride = (size_t)N * N;
-                } else {
-                    out = ws + plane_off + ((size_t)k * 2 + it.s) * N * N + ni;
-                    mstride = N;
-                }
+                // [s][mi][ni/4][k][ni%4] (4 consecutive n of all nodes contiguous).  Bin
+                // q = qb + R2*qa has mi = q + N/2 for qa < R1/2 and q - N/2 after, so
+                // every store is a fixed offset from one of two bases.
                 float sc = ((ni + qb) & 1) ? -scale : scale;     // parity of mi = parity of qb
                 if (it.s) sc = -sc;
                 const bool zero_col = (it.s == 0 && ni == 0);
+                const bool zero_nyq = (it.s == 0 && qb == 0);    // mi = 0 at qa = R1/2
+                auto store_all = [&](float2* out, auto ms_c) {
+                    constexpr size_t MS = decltype(ms_c)::value;
+                    float2* lo = out + (size_t)(qb + N / 2) * MS;
+                    float2* hi = out + (size_t)qb * MS - (size_t)(N / 2) * MS;
 #pragma unroll
-                for (int qa = 0; qa < R1; ++qa) {
-                    const int q = qb + R2 * qa;
-                    const int mi = (q + N / 2) & (N - 1);
-                    float2 val = make_float2(v[qa].x * sc, v[qa].y * sc);
-                    if (zero_col || (it.s == 0 && mi == 0)) val = make_float2(0.f, 0.f);
-                    __stcs(out + (size_t)mi * mstride, val);
-                }
-            } else if (lane == 0 && (warp * 32) >= W * R2) {
+                    for (int qa = 0; qa < R1; ++qa) {
+                        float2 val = make_float2(v[qa].x * sc, v[qa].y * sc);
+                        if (zero_col || (zero_nyq && qa == R1 / 2)) val = make_float2(0.f, 0.f);
+                        float2* dst = (qa < R1 / 2) ? lo + (size_t)R2 * qa * MS : hi + (size_t)R2 * qa * MS;
+                        __stcs(dst, val);
+                    }
+                };
+                if (a.ws_tile_major)
+                    store_all(ws + plane_off + (size_t)it.s * N * N * N + (size_t)(ni >> 2) * N * 4 + (size_t)k * 4 +
+                                  (ni & 3),
+                              std::integral_constant<size_t, (size_t)N * N>());
+                else
+                    store_all(ws + plane_off + ((size_t)k * 2 + it.s) * N * N + ni,
+                              std::integral_constant<size_t, (size_t)N>());
+                        } else if (lane == 0 && (warp * 32) >= W * R2) {
                 mbar_arrive_cta(&empty[b]);
             }
         }
