@@ -314,3 +314,55 @@ def test_forward_tc_mixed_bandwidths(su2):
                     worst = max(worst, abs(o[G.coeff_index(j0 + 2 * i, m2, n2)] - v))
                     scale = max(scale, abs(v))
             assert worst / scale < TOL32
+
+
+@pytest.mark.parametrize("algo", ["fp32", "tc_bf16x3"])
+def test_inverse_n128_vs_oracle(su2, algo):
+    """Synthesis at N = 128 (the two-phase inverse DFT) against the oracle,
+    two functions (the second checks the per-function offsets)."""
+    N = 128
+    rng = np.random.default_rng(14)
+    cs = [cast(I.draw_coeffs(N, rng, "inv1"), "c64") for _ in range(2)]
+    plan = su2.Plan(N=N, batch=2, dtype="c64", algo=algo)
+    g = plan.inverse(to_dev(np.concatenate(cs), "c64"))
+    plan.sync_status()
+    g = g.cpu().numpy().astype(np.complex128)
+    for b in range(2):
+        o = plan.grid_offsets[b]
+        assert rel(g[o:o + N ** 3].reshape(N, N, N), T.inverse_separable(cs[b], N)) < TOL32, b
+
+
+@pytest.mark.parametrize("N,B", [(128, 3), (256, 2), (512, 1)])
+def test_roundtrip_and_adjoint_identity_large(su2, N, B):
+    """Properties that hold at any size, for the two-phase inverse DFT and the
+    fused transposed contraction: recovery within the sector of band-limited
+    single-sector coefficients, forward(inverse(c)) = c there (on the paper's
+    half domain the other sector receives leakage, so only the kept sector is
+    compared), and <A f, g> = <f, A^H g>."""
+    rng = np.random.default_rng(15 + N)
+    plan = su2.Plan(N=N, batch=B, dtype="c64")
+    C = I.num_coeffs(N)
+    two_l = I.packed_two_l(N)
+    cs, keep = [], []
+    for b in range(B):
+        c = I.draw_coeffs(N, rng, "inv1").astype(np.complex64)
+        kept = (two_l % 2) == (b % 2)          # b even: integer l, b odd: half-integer l
+        c[~kept] = 0
+        cs.append(c)
+        keep.append(torch.from_numpy(kept).cuda())
+    c = torch.from_numpy(np.concatenate(cs)).cuda()
+    grid = plan.inverse(c)
+    back = plan.forward(grid)
+    plan.sync_status()
+    for b in range(B):
+        cb, bb = c[b * C:(b + 1) * C][keep[b]], back[b * C:(b + 1) * C][keep[b]]
+        d = (bb - cb).abs().max().item() / cb.abs().max().item()
+        assert d < TOL32, (b, d)
+    f = torch.randn(plan.grid_elems, dtype=torch.complex64, device="cuda")
+    gg = torch.randn(plan.coeff_elems, dtype=torch.complex64, device="cuda")
+    af = plan.forward(f)
+    lhs = torch.vdot(af.to(torch.complex128), gg.to(torch.complex128))
+    rhs = torch.vdot(f.to(torch.complex128), plan.backward(gg).to(torch.complex128))
+    plan.sync_status()
+    scale = (af.abs().double().norm() * gg.abs().double().norm()).item()
+    assert abs((lhs - rhs).item()) < TOL32 * scale
