@@ -23,8 +23,18 @@ def alpha_nodes(N: int, literal: bool = False) -> np.ndarray:
     return -np.pi + h * np.arange(N)
 
 
-def gamma_nodes(N: int, literal: bool = False) -> np.ndarray:
-    """psi_j, same rule as phi_j (Sec. 4, sampling grid)."""
+def gamma_nodes(N: int, literal: bool = False, full: bool = False) -> np.ndarray:
+    """psi_j, same rule as phi_j (Sec. 4, sampling grid).
+
+    full=True: the full-group grid, psi over [-2 pi, 2 pi) with 2N nodes of the
+    same spacing 2 pi/N (psi_j = -2 pi + j * 2 pi/N, j = 0..2N-1).  phi in
+    [-pi, pi) and psi in [-2 pi, 2 pi) cover SU(2) once, so integer and
+    half-integer l are orthogonal there (the paper's domain covers half of it).
+    """
+    if full:
+        if literal:
+            raise ValueError("the full-group grid has the periodic spacing only")
+        return -2.0 * np.pi + (2.0 * np.pi / N) * np.arange(2 * N)
     return alpha_nodes(N, literal)
 
 

@@ -33,6 +33,12 @@ Sector note: on the paper's domain (phi, psi in [-pi, pi]) the integer-l and
 half-integer-l basis functions are not orthogonal to each other, so the forward
 map returns cross-sector leakage for functions that mix both; the oracle
 computes the quadrature sum as defined, leakage included.
+
+Full-group grid (``full=True``): psi in [-2 pi, 2 pi) with 2N nodes, so the
+sampled domain is all of SU(2); the normalised Haar measure is then
+(1/(16 pi^2)) sin(theta) dphi dtheta dpsi and pref = (2 pi/N)^2/(16 pi^2) =
+1/(4N^2).  Grids have shape (N, N, 2N).  On this grid the two sectors are
+orthogonal and band-limited functions mixing both are recovered exactly.
 """
 from __future__ import annotations
 
@@ -41,17 +47,17 @@ import numpy as np
 from . import basis, grid, quadrature
 
 
-def _prefactor(N: int, literal: bool) -> float:
+def _prefactor(N: int, literal: bool, full: bool = False) -> float:
     h = 2.0 * np.pi / ((N - 1) if literal else N)
-    return h * h / (8.0 * np.pi ** 2)
+    return h * h / ((16.0 if full else 8.0) * np.pi ** 2)
 
 
-def _setup(N, weights, literal):
+def _setup(N, weights, literal, full=False):
     al = grid.alpha_nodes(N, literal)
-    ga = grid.gamma_nodes(N, literal)
+    ga = grid.gamma_nodes(N, literal, full)
     be = grid.beta_nodes(N)
     w = quadrature.weights(N, weights)
-    return al, be, ga, w, _prefactor(N, literal)
+    return al, be, ga, w, _prefactor(N, literal, full)
 
 
 def sector_indices(N: int, sector: str) -> np.ndarray:
@@ -78,13 +84,14 @@ def _top_j(N: int, sector: str) -> int:
 # Direct O(N^6) forward and synthesis (t from the group element)
 # ---------------------------------------------------------------------------
 
-def forward_direct(f: np.ndarray, weights: str = "cc", literal: bool = False) -> np.ndarray:
+def forward_direct(f: np.ndarray, weights: str = "cc", literal: bool = False, full: bool = False) -> np.ndarray:
     """Quadrature sum evaluated coefficient by coefficient (Sec. 5).
 
-    f: complex array [j1, k, j2] of shape (N, N, N).  Returns packed coefficients.
+    f: complex array [j1, k, j2] of shape (N, N, N) ((N, N, 2N) on the full-group
+    grid).  Returns packed coefficients.
     """
     N = f.shape[0]
-    al, be, ga, w, pref = _setup(N, weights, literal)
+    al, be, ga, w, pref = _setup(N, weights, literal, full)
     a, b, c, d = basis.u_entries(al[:, None, None], be[None, :, None], ga[None, None, :])
     fw = f * w[None, :, None]
     out = np.zeros(grid.num_coeffs(N), dtype=np.complex128)
@@ -96,13 +103,13 @@ def forward_direct(f: np.ndarray, weights: str = "cc", literal: bool = False) ->
     return out
 
 
-def inverse_direct(coeffs: np.ndarray, N: int, literal: bool = False) -> np.ndarray:
+def inverse_direct(coeffs: np.ndarray, N: int, literal: bool = False, full: bool = False) -> np.ndarray:
     """Synthesis sum_l (2l+1) sum_{m,n} f^(l)_{mn} t^l_{nm} on the grid (Sec. 3)."""
     al = grid.alpha_nodes(N, literal)
-    ga = grid.gamma_nodes(N, literal)
+    ga = grid.gamma_nodes(N, literal, full)
     be = grid.beta_nodes(N)
     a, b, c, d = basis.u_entries(al[:, None, None], be[None, :, None], ga[None, None, :])
-    f = np.zeros((N, N, N), dtype=np.complex128)
+    f = np.zeros((N, N, len(ga)), dtype=np.complex128)
     for j in range(N):
         for m2 in grid.half_range(j):
             for n2 in grid.half_range(j):
@@ -132,7 +139,7 @@ def torus_dft(f: np.ndarray, nvals2: np.ndarray, mvals2: np.ndarray,
 
 
 def forward_separable(f: np.ndarray, weights: str = "cc", literal: bool = False,
-                      row_stride: int = 1) -> np.ndarray:
+                      row_stride: int = 1, full: bool = False) -> np.ndarray:
     """Forward transform by the two-stage separation (Sec. 4 and Sec. 6, k = 1).
 
     Stage 1: f_2(theta_k; m, n) by the torus double sum for every theta_k.
@@ -142,7 +149,7 @@ def forward_separable(f: np.ndarray, weights: str = "cc", literal: bool = False,
     timing sample; the other coefficients stay zero).
     """
     N = f.shape[0]
-    al, be, ga, w, pref = _setup(N, weights, literal)
+    al, be, ga, w, pref = _setup(N, weights, literal, full)
     out = np.zeros(grid.num_coeffs(N), dtype=np.complex128)
     for sector in ("int", "half"):
         idx = sector_indices(N, sector)
@@ -190,11 +197,11 @@ def _torus_synthesis(G: np.ndarray, idx: np.ndarray, alpha, gamma) -> np.ndarray
     return t @ Em
 
 
-def inverse_separable(coeffs: np.ndarray, N: int, literal: bool = False) -> np.ndarray:
+def inverse_separable(coeffs: np.ndarray, N: int, literal: bool = False, full: bool = False) -> np.ndarray:
     """Synthesis (Sec. 3) by separation: theta sum per (n, m), then torus sum."""
     al = grid.alpha_nodes(N, literal)
-    ga = grid.gamma_nodes(N, literal)
-    f = np.zeros((N, N, N), dtype=np.complex128)
+    ga = grid.gamma_nodes(N, literal, full)
+    f = np.zeros((N, N, len(ga)), dtype=np.complex128)
     for sector in ("int", "half"):
         G = _synthesis_planes(coeffs, N, sector, lambda js: (js + 1).astype(np.float64))
         f += _torus_synthesis(G, sector_indices(N, sector), al, ga)
@@ -202,10 +209,10 @@ def inverse_separable(coeffs: np.ndarray, N: int, literal: bool = False) -> np.n
 
 
 def adjoint_separable(g: np.ndarray, N: int, weights: str = "cc",
-                      literal: bool = False) -> np.ndarray:
+                      literal: bool = False, full: bool = False) -> np.ndarray:
     """Conjugate transpose of the forward quadrature map applied to g (packed)."""
-    al, be, ga, w, pref = _setup(N, weights, literal)
-    f = np.zeros((N, N, N), dtype=np.complex128)
+    al, be, ga, w, pref = _setup(N, weights, literal, full)
+    f = np.zeros((N, N, len(ga)), dtype=np.complex128)
     for sector in ("int", "half"):
         G = _synthesis_planes(g, N, sector, lambda js: np.ones(js.shape))
         f += _torus_synthesis(G, sector_indices(N, sector), al, ga)
@@ -217,7 +224,7 @@ def adjoint_separable(g: np.ndarray, N: int, weights: str = "cc",
 # ---------------------------------------------------------------------------
 
 def forward_pair(f: np.ndarray, n2: int, m2: int, weights: str = "cc",
-                 literal: bool = False):
+                 literal: bool = False, full: bool = False):
     """All coefficients f^(l)_{mn}, l = mu..lmax, of one (n, m) pair.
 
     Same definition as ``forward_separable`` restricted to one pair: the torus
@@ -225,7 +232,7 @@ def forward_pair(f: np.ndarray, n2: int, m2: int, weights: str = "cc",
     contraction with the recurrence values.  Returns (j0, values[L]).
     """
     N = f.shape[0]
-    al, be, ga, w, pref = _setup(N, weights, literal)
+    al, be, ga, w, pref = _setup(N, weights, literal, full)
     sector = "int" if n2 % 2 == 0 else "half"
     jtop = _top_j(N, sector)
     en = np.exp(1j * (n2 / 2.0) * al)                    # [j1]
