@@ -112,6 +112,16 @@ typedef struct {
  *   and keeps the fastest.  Results do not depend on the choice. */
 #define SU2_FLAG_CUDA_GRAPH 0x1u
 #define SU2_FLAG_AUTOTUNE 0x2u
+/* SU2_FLAG_FULL_GROUP: grids are sampled on the full group, psi (gamma) over
+ * [-2 pi, 2 pi) with 2N nodes psi_j = -2 pi + 2 pi j/N, so a grid is
+ * f[j1][k][j2] with j2 < 2N (2 N^3 elements per function), and the forward
+ * transform uses the normalised Haar measure of all of SU(2), prefactor
+ * 1/(4N^2).  On the paper's domain (Sec. 4, psi over [-pi, pi]) the integer-l
+ * and half-integer-l sectors are not orthogonal; on the full group they are,
+ * and a band-limited function mixing both sectors is recovered exactly.
+ * complex64, N = 64, 128, 256, forward transform only (su2_inverse and
+ * su2_backward return SU2_ERR_UNSUPPORTED for such plans). */
+#define SU2_FLAG_FULL_GROUP 0x4u
 
 /* Supported bandwidths: N a power of two with 4 <= N <= 512 (c64) and
  * 4 <= N <= 256 (c128).  Anything else returns SU2_ERR_UNSUPPORTED. */

@@ -45,6 +45,7 @@ _lib = None
 # (name, restype, argtypes) for every entry point of include/su2fft.h
 FLAG_CUDA_GRAPH = 0x1
 FLAG_AUTOTUNE = 0x2
+FLAG_FULL_GROUP = 0x4
 
 SIGNATURES = [
     ("su2_plan", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(PlanDesc)]),

@@ -44,6 +44,7 @@ struct Band {
     size_t aux_off = 0;           // stage-1 scratch (two-phase DFT ring) in the workspace
     int aux_ring = 0;
     bool tc = false;              // contraction on tensor cores (tile-major planes)
+    bool full_group = false;      // grids on the full-group grid (forward only)
     int s1_two_phase = 0;         // kernel choices (defaults, or the autotuner's)
     int s2_bt = 0;
 };
@@ -238,7 +239,8 @@ su2::BandArgs band_args(const su2_plan_s* P, const Band& b) {
     a.ws_tile_major = b.tc ? 1 : 0;
     a.s1_two_phase = b.s1_two_phase;
     a.s2_bt = b.s2_bt;
-    const size_t n3 = (size_t)b.N * b.N * b.N;
+    a.full_group = b.full_group ? 1 : 0;
+    const size_t n3 = (b.full_group ? 2 : 1) * (size_t)b.N * b.N * b.N;   // elements of one grid
     for (size_t i = 0; i < b.fids.size(); ++i)
         if (P->grid_off[b.fids[i]] != a.grid_group_off + i * n3) a.grid_regular = 0;
     return a;
@@ -337,7 +339,7 @@ cudaError_t autotune(su2_plan_s* P) {
     for (auto& kv : P->bands) {
         Band& b = kv.second;
         const int N = kv.first;
-        const bool try_s1 = b.aux_ring > 0 && !b.tc && (N == 64 || N == 128);
+        const bool try_s1 = b.aux_ring > 0 && !b.tc && !b.full_group && (N == 64 || N == 128);
         const bool try_s2 = !b.tc;
         if (!try_s1 && !try_s2) continue;
         const int nb = std::min((int)b.fids.size(), 32);
@@ -447,8 +449,11 @@ const char* su2_status_string(su2_status s) {
 
 su2_status su2_plan(su2_plan_t* out, const su2_plan_desc* desc) {
     if (!out || !desc) return SU2_ERR_INVALID_ARG;
-    if (desc->num_functions < 1 || (desc->flags & ~(SU2_FLAG_CUDA_GRAPH | SU2_FLAG_AUTOTUNE)) != 0)
+    if (desc->num_functions < 1 ||
+        (desc->flags & ~(SU2_FLAG_CUDA_GRAPH | SU2_FLAG_AUTOTUNE | SU2_FLAG_FULL_GROUP)) != 0)
         return SU2_ERR_INVALID_ARG;
+    const bool full_group = (desc->flags & SU2_FLAG_FULL_GROUP) != 0;
+    if (full_group && desc->dtype != SU2_C64) return SU2_ERR_UNSUPPORTED;
     if (desc->dtype != SU2_C64 && desc->dtype != SU2_C128) return SU2_ERR_INVALID_ARG;
     if (desc->weights != SU2_WEIGHTS_CC && desc->weights != SU2_WEIGHTS_RIEMANN) return SU2_ERR_INVALID_ARG;
     su2_algo algo = desc->algo;
@@ -460,6 +465,7 @@ su2_status su2_plan(su2_plan_t* out, const su2_plan_desc* desc) {
     for (int f = 0; f < desc->num_functions; ++f) {
         const int N = desc->N ? desc->N[f] : desc->N_uniform;
         if (!is_pow2(N) || N < 4 || N > Nmax_allowed) return SU2_ERR_UNSUPPORTED;
+        if (full_group && (N < 64 || N > 256)) return SU2_ERR_UNSUPPORTED;
         Ns[f] = N;
     }
     int ndev = 0;
@@ -493,7 +499,7 @@ su2_status su2_plan(su2_plan_t* out, const su2_plan_desc* desc) {
         const size_t N = (size_t)kv.first;
         for (int f : kv.second.fids) {
             P->grid_off[f] = P->grid_total;
-            P->grid_total += N * N * N;
+            P->grid_total += (full_group ? 2 : 1) * N * N * N;
         }
     }
     // stage-1 planes: contiguous per bandwidth group, functions in batch order,
@@ -510,17 +516,18 @@ su2_status su2_plan(su2_plan_t* out, const su2_plan_desc* desc) {
         kv.second.tc = algo == SU2_ALGO_TC_BF16X3 && su2::tc_supported(kv.first);
         // complex64 at N >= 128; the tensor-core path also at N = 64 (its planes are tile-major)
         if (!su2::fft_forward_two_phase_supported(kv.first, desc->dtype == SU2_C128)) continue;
-        if (kv.first < 128 && !kv.second.tc && !(desc->flags & SU2_FLAG_AUTOTUNE)) continue;
+        if (kv.first < 128 && !kv.second.tc && !(desc->flags & SU2_FLAG_AUTOTUNE) && !full_group) continue;
         size_t elems = 0;
         int ring = 0;
-        const cudaError_t ea = su2::fft_forward_aux(kv.first, desc->device, &ring, &elems);
+        const cudaError_t ea = su2::fft_forward_aux(kv.first, desc->device, full_group, &ring, &elems);
         if (ea != cudaSuccess) {
             delete P;
             return from_cuda(ea);
         }
         kv.second.aux_off = P->ws_total;
         kv.second.aux_ring = ring;
-        kv.second.s1_two_phase = (kv.first >= 128 || kv.second.tc) ? 1 : 0;
+        kv.second.s1_two_phase = (kv.first >= 128 || kv.second.tc || full_group) ? 1 : 0;
+        kv.second.full_group = full_group;
         P->ws_total += elems;
     }
     std::vector<double> lf2(2 * Nmax + 2);
@@ -643,6 +650,7 @@ static su2_status run_transpose(su2_plan_t plan, su2::TransposeMode mode, const 
                                 void* ws, void* stream) {
     su2_status s = check_exec(plan, coeffs, grid, ws);
     if (s != SU2_OK) return s;
+    if (plan->flags & SU2_FLAG_FULL_GROUP) return SU2_ERR_UNSUPPORTED;     // forward only
     DeviceGuard g(plan->device);
     if (!g.ok) return SU2_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;

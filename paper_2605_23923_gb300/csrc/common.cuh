@@ -314,6 +314,7 @@ struct BandArgs {
                                   // (tensor-core plans), 0: [k][s][mi][ni]
     int s1_two_phase;             // forward 2-D DFT: 1 two-phase kernel (needs aux_ring > 0), 0 cluster
     int s2_bt;                    // FP32 forward contraction: functions per block (8 or 16; 0: by batch)
+    int full_group;               // grids on the full-group grid (psi over [-2 pi, 2 pi), 2N nodes)
 };
 
 }  // namespace su2

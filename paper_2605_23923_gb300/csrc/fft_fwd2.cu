@@ -24,6 +24,11 @@
 // progress whatever number of its CTAs is resident; every wait is also bounded
 // (it latches the error word and gives up).
 //
+// Full-group grid (psi over [-2 pi, 2 pi), 2N nodes; template FULL): an A item
+// loads both psi halves of its 16 columns and folds them, x + x' for integer m
+// and (x - x') e^{i pi j2/N} for half-integer m (the 2N-point psi sum reduced to
+// N points); weight w_k/(4N^2); origin phase (-1)^n and i (-1)^{n0}.
+//
 // CTA layout: warps 0 .. CT/32-1 compute, one producer warp issues the loads
 // (after the dependency waits) into a two-slot ring; mbarriers full/empty.
 #include <cuda.h>
@@ -40,7 +45,7 @@
 namespace su2 {
 namespace fwd2 {
 
-template <int N>
+template <int N, bool FULL = false>
 struct Cfg {
     static constexpr int R1 = Radix<N>::R1, R2 = Radix<N>::R2;
     static constexpr int W = 16;                        // columns per A item, rows per B item
@@ -50,13 +55,16 @@ struct Cfg {
     static constexpr int THREADS = CT + 32;
     static constexpr int SLOT = W * N;                  // float2 of an A slab / B block
     static constexpr int PB = N + 1;                    // row pitch of a B block in the slot
-    static constexpr int SLOTP = SLOT + 16;             // slot stride (B pitch padding; 128-B multiple)
+    static constexpr int YP = SLOT + 16;                // B block with its pitch padding (128-B multiple)
+    // full-group grid: an A slab holds both psi halves (columns j2 and j2 + N)
+    static constexpr int SLOTP = (FULL ? 2 * SLOT : SLOT) + 16;   // slot stride
     static constexpr int NS = 2;                        // ring slots
     static constexpr int BOXR = N < 256 ? N : 256;      // rows per TMA box (at most 256)
     static constexpr size_t smem_bytes() {
-        return (size_t)(NS + 1) * SLOTP * 8 + (size_t)N * 8 * 2 + (size_t)N * 4 + 2 * NS * 8 + NS * 4;
+        return (size_t)NS * SLOTP * 8 + (size_t)YP * 8 + (size_t)N * 8 * 2 + (size_t)N * 4 + 2 * NS * 8 + NS * 4;
     }
-    static constexpr int BLOCKS_PER_SM = (N <= 64) ? 4 : (N <= 128) ? 3 : (N <= 256 ? 2 : 1);
+    static constexpr int BLOCKS_PER_SM =
+        FULL ? (N <= 128 ? 2 : 1) : ((N <= 64) ? 4 : (N <= 128) ? 3 : (N <= 256 ? 2 : 1));
 };
 
 __device__ __forceinline__ void tma_load_3d_hint(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
@@ -133,16 +141,16 @@ __device__ __forceinline__ Item decode(int i, int nplanes, int D) {
     return it;
 }
 
-template <int N>
-__global__ void __launch_bounds__(Cfg<N>::THREADS, Cfg<N>::BLOCKS_PER_SM)
+template <int N, bool FULL>
+__global__ void __launch_bounds__(Cfg<N, FULL>::THREADS, Cfg<N, FULL>::BLOCKS_PER_SM)
 fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const float2* __restrict__ grid,
                   float2* __restrict__ ws, int D, int RING, int discard_ok) {
-    using P = Cfg<N>;
+    using P = Cfg<N, FULL>;
     constexpr int R1 = P::R1, R2 = P::R2, W = P::W, CT = P::CT, SLOT = P::SLOT, NS = P::NS;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float2* S = reinterpret_cast<float2*>(smem_raw);          // [NS][SLOT] ring
     float2* Y = S + NS * P::SLOTP;                             // sector-1 columns of an A item
-    float2* om = Y + P::SLOTP;                                 // exp(+2 pi i t/N)
+    float2* om = Y + P::YP;                                    // exp(+2 pi i t/N)
     float2* tw = om + N;                                       // exp(+i pi t/N)
     float* wk = reinterpret_cast<float*>(tw + N);
     uint64_t* full = reinterpret_cast<uint64_t*>(wk + N);      // [NS]
@@ -206,20 +214,26 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
             if (it.isA) {
                 const int fb = it.plane / N, k = it.plane % N;
                 if (lane == 0 && use > 0) wait_counter(&doneB[r], use * P::NB, a.err);
+                constexpr int NSL = FULL ? 2 : 1;                 // slabs per A item
+                constexpr int GN = FULL ? 2 * N : N;              // psi nodes of a grid row
                 if (a.grid_regular) {
                     if (lane == 0) {
-                        mbar_arrive_expect_tx(&full[b], (uint32_t)(SLOT * 8));
+                        mbar_arrive_expect_tx(&full[b], (uint32_t)(NSL * SLOT * 8));
 #pragma unroll
-                        for (int h = 0; h < N / P::BOXR; ++h)
-                            tma_load_3d_hint(dst + h * P::BOXR * W, &gmap, it.jb * W, k, fb * N + h * P::BOXR,
-                                             &full[b], pol);
+                        for (int sl = 0; sl < NSL; ++sl)
+#pragma unroll
+                            for (int h = 0; h < N / P::BOXR; ++h)
+                                tma_load_3d_hint(dst + sl * SLOT + h * P::BOXR * W, &gmap, it.jb * W + sl * N, k,
+                                                 fb * N + h * P::BOXR, &full[b], pol);
                     }
                 } else {
-                    const float2* src = grid + a.grid_off[a.fidx[fb]] + (size_t)k * N + it.jb * W;
-                    if (lane == 0) mbar_arrive_expect_tx(&full[b], (uint32_t)(SLOT * 8));
+                    const float2* src = grid + a.grid_off[a.fidx[fb]] + (size_t)k * GN + it.jb * W;
+                    if (lane == 0) mbar_arrive_expect_tx(&full[b], (uint32_t)(NSL * SLOT * 8));
                     __syncwarp();
-                    for (int j1 = lane; j1 < N; j1 += 32)
-                        bulk_g2s(dst + j1 * W, src + (size_t)j1 * N * N, (uint32_t)(W * 8), &full[b]);
+                    for (int sl = 0; sl < NSL; ++sl)
+                        for (int j1 = lane; j1 < N; j1 += 32)
+                            bulk_g2s(dst + sl * SLOT + j1 * W, src + sl * N + (size_t)j1 * N * GN, (uint32_t)(W * 8),
+                                     &full[b]);
                 }
             } else if (lane == 0) {
                 // B item: the compute threads read the rows from L2 themselves; the
@@ -254,8 +268,15 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
                 float2 v[R2], w[R2];
 #pragma unroll
                 for (int q = 0; q < R2; ++q) {
-                    v[q] = X[(ia + R1 * q) * W + jc];
-                    w[q] = cmul(v[q], tw[ia + R1 * q]);
+                    if constexpr (FULL) {
+                        // fold the two psi halves: integer m sees x + x', half-integer m (x - x') e^{i pi j2/N}
+                        const float2 x0 = X[(ia + R1 * q) * W + jc], x1 = X[SLOT + (ia + R1 * q) * W + jc];
+                        v[q] = make_float2(x0.x + x1.x, x0.y + x1.y);
+                        w[q] = cmul(make_float2(x0.x - x1.x, x0.y - x1.y), tw[ia + R1 * q]);
+                    } else {
+                        v[q] = X[(ia + R1 * q) * W + jc];
+                        w[q] = cmul(v[q], tw[ia + R1 * q]);
+                    }
                 }
                 dft_reg<R2, 1, float>(w);
 #pragma unroll
@@ -332,7 +353,7 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
                 named_sync(2, W * R2);
                 if (lane == 0) mbar_arrive_cta(&empty[b]);
                 dft_reg<R1, 1, float>(v);
-                const float scale = wk[k] / (2.f * (float)N * (float)N);
+                const float scale = wk[k] / ((FULL ? 4.f : 2.f) * (float)N * (float)N);
                 const size_t plane_off = a.grid_regular ? a.ws_group_off + (size_t)fb * 2 * N * N * N
                                                         : a.ws_off[a.fidx[fb]];
                 const int p = it.pb * W + pl;
@@ -341,8 +362,17 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
                 // [s][mi][ni/4][k][ni%4] (4 consecutive n of all nodes contiguous).  Bin
                 // q = qb + R2*qa has mi = q + N/2 for qa < R1/2 and q - N/2 after, so
                 // every store is a fixed offset from one of two bases.
-                float sc = ((ni + qb) & 1) ? -scale : scale;     // parity of mi = parity of qb
-                if (it.s) sc = -sc;
+                // phase of the grid origin: (-1)^{n+m} (sector 0) and -(-1)^{n0+m0}
+                // (sector 1, n = n0 + 1/2) on the paper's domain; on the full-group grid
+                // (psi from -2 pi) (-1)^n and i (-1)^{n0}
+                float sc;
+                if constexpr (FULL) {
+                    sc = (ni & 1) ? -scale : scale;
+                } else {
+                    sc = ((ni + qb) & 1) ? -scale : scale;     // parity of mi = parity of qb
+                    if (it.s) sc = -sc;
+                }
+                const bool rot = FULL && it.s;                   // times i
                 const bool zero_col = (it.s == 0 && ni == 0);
                 const bool zero_nyq = (it.s == 0 && qb == 0);    // mi = 0 at qa = R1/2
                 auto store_all = [&](float2* out, auto ms_c) {
@@ -351,7 +381,8 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
                     float2* hi = out + (size_t)qb * MS - (size_t)(N / 2) * MS;
 #pragma unroll
                     for (int qa = 0; qa < R1; ++qa) {
-                        float2 val = make_float2(v[qa].x * sc, v[qa].y * sc);
+                        float2 val = rot ? make_float2(-v[qa].y * sc, v[qa].x * sc)
+                                         : make_float2(v[qa].x * sc, v[qa].y * sc);
                         if (zero_col || (zero_nyq && qa == R1 / 2)) val = make_float2(0.f, 0.f);
                         float2* dst = (qa < R1 / 2) ? lo + (size_t)R2 * qa * MS : hi + (size_t)R2 * qa * MS;
                         __stcs(dst, val);
@@ -372,13 +403,13 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
 }
 
 // Work-distribution parameters shared by the plan (workspace size) and the launch.
-template <int N>
+template <int N, bool FULL>
 static cudaError_t geometry(int device, int* G, int* D, int* RING) {
-    using P = Cfg<N>;
+    using P = Cfg<N, FULL>;
     int sms = 0, per = 0;
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) return e;
-    auto kern = fft_fwd_two_phase<N>;
+    auto kern = fft_fwd_two_phase<N, FULL>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::smem_bytes());
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, P::THREADS, P::smem_bytes());
@@ -391,13 +422,13 @@ static cudaError_t geometry(int device, int* G, int* D, int* RING) {
     return cudaSuccess;
 }
 
-template <int N>
+template <int N, bool FULL>
 static cudaError_t launch_n(const BandArgs& a, const void* in, void* out, cudaStream_t st) {
-    using P = Cfg<N>;
+    using P = Cfg<N, FULL>;
     int dev = 0, G = 0, D = 0, RING = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if ((e = geometry<N>(dev, &G, &D, &RING)) != cudaSuccess) return e;
+    if ((e = geometry<N, FULL>(dev, &G, &D, &RING)) != cudaSuccess) return e;
     if (RING != a.aux_ring) return cudaErrorInvalidValue;          // plan built for another device shape
     float2* ring = (float2*)out + a.ws_aux_off;
     unsigned* ctr = reinterpret_cast<unsigned*>(ring + (size_t)RING * 2 * N * N);
@@ -406,8 +437,9 @@ static cudaError_t launch_n(const BandArgs& a, const void* in, void* out, cudaSt
     memset(&gmap, 0, sizeof(gmap));
     BandArgs b = a;
     if (b.grid_regular) {
-        const cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)a.nfunc * N};
-        const cuuint64_t strides[2] = {(cuuint64_t)N * 8, (cuuint64_t)N * N * 8};
+        constexpr int GN = FULL ? 2 * N : N;                      // psi nodes per grid row
+        const cuuint64_t dims[3] = {(cuuint64_t)GN, (cuuint64_t)N, (cuuint64_t)a.nfunc * N};
+        const cuuint64_t strides[2] = {(cuuint64_t)GN * 8, (cuuint64_t)N * GN * 8};
         const cuuint32_t box[3] = {(cuuint32_t)P::W, 1, (cuuint32_t)P::BOXR};
         const void* base = (const float2*)in + a.grid_group_off;
         if (!encode_tensor_map_8b(&gmap, 3, base, dims, strides, box)) b.grid_regular = 0;
@@ -421,8 +453,8 @@ static cudaError_t launch_n(const BandArgs& a, const void* in, void* out, cudaSt
         if (c >= 1 && c < grid) grid = c;
     }
     const int discard_ok = ((uintptr_t)ring % 128) == 0;
-    fft_fwd_two_phase<N><<<grid, P::THREADS, P::smem_bytes(), st>>>(b, gmap, (const float2*)in, (float2*)out, D,
-                                                                   RING, discard_ok);
+    fft_fwd_two_phase<N, FULL><<<grid, P::THREADS, P::smem_bytes(), st>>>(b, gmap, (const float2*)in, (float2*)out,
+                                                                         D, RING, discard_ok);
     return cudaGetLastError();
 }
 
@@ -430,15 +462,24 @@ static cudaError_t launch_n(const BandArgs& a, const void* in, void* out, cudaSt
 
 bool fft_forward_two_phase_supported(int N, bool fp64) { return !fp64 && (N == 64 || N == 128 || N == 256 || N == 512); }
 
-cudaError_t fft_forward_aux(int N, int device, int* ring, size_t* elems) {
+cudaError_t fft_forward_aux(int N, int device, bool full_group, int* ring, size_t* elems) {
     int G = 0, D = 0, R = 0;
     cudaError_t e;
-    switch (N) {
-        case 64: e = fwd2::geometry<64>(device, &G, &D, &R); break;
-        case 128: e = fwd2::geometry<128>(device, &G, &D, &R); break;
-        case 256: e = fwd2::geometry<256>(device, &G, &D, &R); break;
-        case 512: e = fwd2::geometry<512>(device, &G, &D, &R); break;
-        default: return cudaErrorInvalidValue;
+    if (full_group) {
+        switch (N) {
+            case 64: e = fwd2::geometry<64, true>(device, &G, &D, &R); break;
+            case 128: e = fwd2::geometry<128, true>(device, &G, &D, &R); break;
+            case 256: e = fwd2::geometry<256, true>(device, &G, &D, &R); break;
+            default: return cudaErrorInvalidValue;
+        }
+    } else {
+        switch (N) {
+            case 64: e = fwd2::geometry<64, false>(device, &G, &D, &R); break;
+            case 128: e = fwd2::geometry<128, false>(device, &G, &D, &R); break;
+            case 256: e = fwd2::geometry<256, false>(device, &G, &D, &R); break;
+            case 512: e = fwd2::geometry<512, false>(device, &G, &D, &R); break;
+            default: return cudaErrorInvalidValue;
+        }
     }
     if (e != cudaSuccess) return e;
     *ring = R;
@@ -450,11 +491,19 @@ cudaError_t fft_forward_aux(int N, int device, int* ring, size_t* elems) {
 
 cudaError_t launch_fft_forward_two_phase(const BandArgs& a, const void* grid, void* ws, cudaStream_t st) {
     if (a.nfunc <= 0) return cudaSuccess;
+    if (a.full_group) {
+        switch (a.N) {
+            case 64: return fwd2::launch_n<64, true>(a, grid, ws, st);
+            case 128: return fwd2::launch_n<128, true>(a, grid, ws, st);
+            case 256: return fwd2::launch_n<256, true>(a, grid, ws, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (a.N) {
-        case 64: return fwd2::launch_n<64>(a, grid, ws, st);
-        case 128: return fwd2::launch_n<128>(a, grid, ws, st);
-        case 256: return fwd2::launch_n<256>(a, grid, ws, st);
-        case 512: return fwd2::launch_n<512>(a, grid, ws, st);
+        case 64: return fwd2::launch_n<64, false>(a, grid, ws, st);
+        case 128: return fwd2::launch_n<128, false>(a, grid, ws, st);
+        case 256: return fwd2::launch_n<256, false>(a, grid, ws, st);
+        case 512: return fwd2::launch_n<512, false>(a, grid, ws, st);
         default: return cudaErrorInvalidValue;
     }
 }

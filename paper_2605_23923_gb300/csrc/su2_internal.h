@@ -17,7 +17,7 @@ cudaError_t launch_fft_forward(const BandArgs& a, bool fp64, const void* grid, v
 // Two-phase complex64 forward DFT (N = 64, 128, 256, 512): its scratch ring
 // (plane slots and size in complex elements, for the plan's workspace) and launch.
 bool fft_forward_two_phase_supported(int N, bool fp64);
-cudaError_t fft_forward_aux(int N, int device, int* ring, size_t* elems);
+cudaError_t fft_forward_aux(int N, int device, bool full_group, int* ring, size_t* elems);
 cudaError_t launch_fft_forward_two_phase(const BandArgs& a, const void* grid, void* ws, cudaStream_t st);
 // Two-phase complex64 inverse DFT (N = 128, 256, 512) over the tile-major
 // planes, using the forward's scratch ring.

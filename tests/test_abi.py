@@ -68,6 +68,10 @@ def test_plan_validation_on_host(lib):
     assert lib.su2_plan(ctypes.byref(h), ctypes.byref(_desc(N=512, dtype=1))) == 2   # c128 limit
     assert lib.su2_plan(ctypes.byref(h), ctypes.byref(_desc(dtype=0, algo=1))) == 2   # FP64 needs c128
     assert lib.su2_plan(ctypes.byref(h), ctypes.byref(_desc(dtype=1, algo=2))) == 2
+    # full-group grid: complex64, N = 64..256 only
+    assert lib.su2_plan(ctypes.byref(h), ctypes.byref(_desc(N=32, dtype=0, algo=2, flags=0x4))) == 2
+    assert lib.su2_plan(ctypes.byref(h), ctypes.byref(_desc(N=512, dtype=0, algo=2, flags=0x4))) == 2
+    assert lib.su2_plan(ctypes.byref(h), ctypes.byref(_desc(N=64, dtype=1, algo=1, flags=0x4))) == 2
 
 
 def test_null_plan_calls(lib):
