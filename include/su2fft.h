@@ -122,6 +122,16 @@ typedef struct {
  * complex64, N = 64, 128, 256, forward transform only (su2_inverse and
  * su2_backward return SU2_ERR_UNSUPPORTED for such plans). */
 #define SU2_FLAG_FULL_GROUP 0x4u
+/* SU2_FLAG_LITERAL_GRID: grids are sampled on the grid as Sec. 4 prints it,
+ * alpha_j = gamma_j = -pi + 2 pi j/(N-1), j = 0..N-1 (the last node, +pi,
+ * repeats the first), beta_k unchanged; the forward transform carries the cell
+ * (2 pi/(N-1))^2, prefactor 1/(2(N-1)^2).  Grids keep the N^3 layout.  The
+ * repeated node is folded onto the first and the (N-1)-point DFTs are taken
+ * as dense products, so stage 1 costs O(N^4) per function instead of
+ * O(N^3 log N).  complex64, any supported N, forward transform only
+ * (su2_inverse and su2_backward return SU2_ERR_UNSUPPORTED); combined with
+ * SU2_FLAG_FULL_GROUP it is SU2_ERR_INVALID_ARG. */
+#define SU2_FLAG_LITERAL_GRID 0x8u
 
 /* Supported bandwidths: N a power of two with 4 <= N <= 512 (c64) and
  * 4 <= N <= 256 (c128).  Anything else returns SU2_ERR_UNSUPPORTED. */

@@ -41,7 +41,7 @@ class Plan:
 
     def __init__(self, N=None, batch: int = 1, dtype: str = "c64", algo: str = "auto",
                  weights: str = "cc", device: int | None = None, Ns=None, graph: bool = False,
-                 autotune: bool = False, full_group: bool = False):
+                 autotune: bool = False, full_group: bool = False, literal: bool = False):
         self._lib = load()
         if Ns is not None:
             Ns = [int(n) for n in Ns]
@@ -65,8 +65,9 @@ class Plan:
         desc.algo = _abi.ALGOS[algo]
         desc.weights = _abi.WEIGHTS[weights]
         desc.flags = ((_abi.FLAG_CUDA_GRAPH if graph else 0) | (_abi.FLAG_AUTOTUNE if autotune else 0) |
-                      (_abi.FLAG_FULL_GROUP if full_group else 0))
+                      (_abi.FLAG_FULL_GROUP if full_group else 0) | (_abi.FLAG_LITERAL_GRID if literal else 0))
         self.full_group = full_group
+        self.literal = literal
         desc.device = self.device
         h = ctypes.c_void_p()
         _abi.check("su2_plan", self._lib.su2_plan(ctypes.byref(h), ctypes.byref(desc)))

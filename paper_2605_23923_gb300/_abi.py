@@ -46,6 +46,7 @@ _lib = None
 FLAG_CUDA_GRAPH = 0x1
 FLAG_AUTOTUNE = 0x2
 FLAG_FULL_GROUP = 0x4
+FLAG_LITERAL_GRID = 0x8
 
 SIGNATURES = [
     ("su2_plan", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(PlanDesc)]),

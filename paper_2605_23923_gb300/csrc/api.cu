@@ -45,6 +45,9 @@ struct Band {
     int aux_ring = 0;
     bool tc = false;              // contraction on tensor cores (tile-major planes)
     bool full_group = false;      // grids on the full-group grid (forward only)
+    bool literal = false;         // grids on the printed grid (forward only)
+    float2* d_lit_w = nullptr;
+    float2* d_lit_twist = nullptr;
     int s1_two_phase = 0;         // kernel choices (defaults, or the autotuner's)
     int s2_bt = 0;
 };
@@ -207,6 +210,23 @@ cudaError_t build_band(su2_plan_s* P, Band& b) {
     if ((e = P->upload(&b.d_om64, om64.data(), N)) != cudaSuccess) return e;
     if ((e = P->upload(&b.d_twist32, tw32.data(), N)) != cudaSuccess) return e;
     if ((e = P->upload(&b.d_twist64, tw64.data(), N)) != cudaSuccess) return e;
+    if (b.literal) {
+        // (N-1)-point DFT matrix at the output frequencies r - N/2 and the half-bin twist
+        const int M = N - 1;
+        std::vector<float2> W((size_t)N * N), lt(2 * N);
+        for (int r = 0; r < N; ++r)
+            for (int t = 0; t < N; ++t) {
+                const long q = ((long)(r - N / 2) * t) % M;          // exact phase reduction
+                const double a = 2.0 * M_PI * (double)q / M;
+                W[(size_t)r * N + t] = t < M ? make_float2((float)cos(a), (float)sin(a)) : make_float2(0.f, 0.f);
+            }
+        for (int u = 0; u < 2 * N; ++u) {
+            const double a = M_PI * u / M;
+            lt[u] = make_float2((float)cos(a), (float)sin(a));
+        }
+        if ((e = P->upload(&b.d_lit_w, W.data(), W.size())) != cudaSuccess) return e;
+        if ((e = P->upload(&b.d_lit_twist, lt.data(), lt.size())) != cudaSuccess) return e;
+    }
     return cudaSuccess;
 }
 
@@ -240,6 +260,9 @@ su2::BandArgs band_args(const su2_plan_s* P, const Band& b) {
     a.s1_two_phase = b.s1_two_phase;
     a.s2_bt = b.s2_bt;
     a.full_group = b.full_group ? 1 : 0;
+    a.literal = b.literal ? 1 : 0;
+    a.lit_w = b.d_lit_w;
+    a.lit_twist = b.d_lit_twist;
     const size_t n3 = (b.full_group ? 2 : 1) * (size_t)b.N * b.N * b.N;   // elements of one grid
     for (size_t i = 0; i < b.fids.size(); ++i)
         if (P->grid_off[b.fids[i]] != a.grid_group_off + i * n3) a.grid_regular = 0;
@@ -339,7 +362,7 @@ cudaError_t autotune(su2_plan_s* P) {
     for (auto& kv : P->bands) {
         Band& b = kv.second;
         const int N = kv.first;
-        const bool try_s1 = b.aux_ring > 0 && !b.tc && !b.full_group && (N == 64 || N == 128);
+        const bool try_s1 = b.aux_ring > 0 && !b.tc && !b.full_group && !b.literal && (N == 64 || N == 128);
         const bool try_s2 = !b.tc;
         if (!try_s1 && !try_s2) continue;
         const int nb = std::min((int)b.fids.size(), 32);
@@ -450,10 +473,12 @@ const char* su2_status_string(su2_status s) {
 su2_status su2_plan(su2_plan_t* out, const su2_plan_desc* desc) {
     if (!out || !desc) return SU2_ERR_INVALID_ARG;
     if (desc->num_functions < 1 ||
-        (desc->flags & ~(SU2_FLAG_CUDA_GRAPH | SU2_FLAG_AUTOTUNE | SU2_FLAG_FULL_GROUP)) != 0)
+        (desc->flags & ~(SU2_FLAG_CUDA_GRAPH | SU2_FLAG_AUTOTUNE | SU2_FLAG_FULL_GROUP | SU2_FLAG_LITERAL_GRID)) != 0)
         return SU2_ERR_INVALID_ARG;
     const bool full_group = (desc->flags & SU2_FLAG_FULL_GROUP) != 0;
-    if (full_group && desc->dtype != SU2_C64) return SU2_ERR_UNSUPPORTED;
+    const bool literal = (desc->flags & SU2_FLAG_LITERAL_GRID) != 0;
+    if (full_group && literal) return SU2_ERR_INVALID_ARG;             // two different grids
+    if ((full_group || literal) && desc->dtype != SU2_C64) return SU2_ERR_UNSUPPORTED;
     if (desc->dtype != SU2_C64 && desc->dtype != SU2_C128) return SU2_ERR_INVALID_ARG;
     if (desc->weights != SU2_WEIGHTS_CC && desc->weights != SU2_WEIGHTS_RIEMANN) return SU2_ERR_INVALID_ARG;
     su2_algo algo = desc->algo;
@@ -511,9 +536,23 @@ su2_status su2_plan(su2_plan_t* out, const su2_plan_desc* desc) {
             P->ws_total += 2 * N * N * N;
         }
     }
-    // scratch of the two-phase stage-1 DFT, after all planes
+    // scratch of the two-phase stage-1 DFT (or of the literal-grid DFT), after all planes
     for (auto& kv : P->bands) {
         kv.second.tc = algo == SU2_ALGO_TC_BF16X3 && su2::tc_supported(kv.first);
+        if (literal) {
+            size_t elems = 0;
+            int ctas = 0;
+            const cudaError_t ea = su2::fft_forward_literal_aux(kv.first, desc->device, &ctas, &elems);
+            if (ea != cudaSuccess) {
+                delete P;
+                return from_cuda(ea);
+            }
+            kv.second.literal = true;
+            kv.second.aux_off = P->ws_total;
+            kv.second.aux_ring = ctas;
+            P->ws_total += elems;
+            continue;
+        }
         // complex64 at N >= 128; the tensor-core path also at N = 64 (its planes are tile-major)
         if (!su2::fft_forward_two_phase_supported(kv.first, desc->dtype == SU2_C128)) continue;
         if (kv.first < 128 && !kv.second.tc && !(desc->flags & SU2_FLAG_AUTOTUNE) && !full_group) continue;
@@ -650,7 +689,7 @@ static su2_status run_transpose(su2_plan_t plan, su2::TransposeMode mode, const 
                                 void* ws, void* stream) {
     su2_status s = check_exec(plan, coeffs, grid, ws);
     if (s != SU2_OK) return s;
-    if (plan->flags & SU2_FLAG_FULL_GROUP) return SU2_ERR_UNSUPPORTED;     // forward only
+    if (plan->flags & (SU2_FLAG_FULL_GROUP | SU2_FLAG_LITERAL_GRID)) return SU2_ERR_UNSUPPORTED;   // forward only
     DeviceGuard g(plan->device);
     if (!g.ok) return SU2_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;

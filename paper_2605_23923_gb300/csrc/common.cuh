@@ -315,6 +315,10 @@ struct BandArgs {
     int s1_two_phase;             // forward 2-D DFT: 1 two-phase kernel (needs aux_ring > 0), 0 cluster
     int s2_bt;                    // FP32 forward contraction: functions per block (8 or 16; 0: by batch)
     int full_group;               // grids on the full-group grid (psi over [-2 pi, 2 pi), 2N nodes)
+    int literal;                  // grids on the printed grid (spacing 2 pi/(N-1), endpoint repeated);
+                                  // aux_ring then counts the literal kernel's CTAs (one N^2 slab each)
+    const float2* lit_w;          // [N][N] e^{2 pi i (r - N/2) t/(N-1)}, column N-1 zero (literal grid)
+    const float2* lit_twist;      // [2N] e^{i pi u/(N-1)} (literal grid)
 };
 
 }  // namespace su2

@@ -918,6 +918,7 @@ static cudaError_t launch_any(const BandArgs& a, const void* in, void* out, cuda
 }
 
 cudaError_t launch_fft_forward(const BandArgs& a, bool fp64, const void* grid, void* ws, cudaStream_t st) {
+    if (a.literal) return fp64 ? cudaErrorInvalidValue : launch_fft_forward_literal(a, grid, ws, st);
     if (a.aux_ring > 0 && a.s1_two_phase && fft_forward_two_phase_supported(a.N, fp64))
         return launch_fft_forward_two_phase(a, grid, ws, st);
     return fp64 ? launch_any<double, true>(a, grid, ws, st) : launch_any<float, true>(a, grid, ws, st);

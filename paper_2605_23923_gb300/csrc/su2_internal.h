@@ -19,6 +19,10 @@ cudaError_t launch_fft_forward(const BandArgs& a, bool fp64, const void* grid, v
 bool fft_forward_two_phase_supported(int N, bool fp64);
 cudaError_t fft_forward_aux(int N, int device, bool full_group, int* ring, size_t* elems);
 cudaError_t launch_fft_forward_two_phase(const BandArgs& a, const void* grid, void* ws, cudaStream_t st);
+// Complex64 forward DFT on the printed grid (endpoint folded, (N-1)-point DFTs as
+// dense products): CTAs and per-CTA scratch (complex elements), and launch.
+cudaError_t fft_forward_literal_aux(int N, int device, int* ctas, size_t* elems);
+cudaError_t launch_fft_forward_literal(const BandArgs& a, const void* grid, void* ws, cudaStream_t st);
 // Two-phase complex64 inverse DFT (N = 128, 256, 512) over the tile-major
 // planes, using the forward's scratch ring.
 bool fft_inverse_two_phase_supported(int N, bool fp64);

@@ -72,6 +72,9 @@ def test_plan_validation_on_host(lib):
     assert lib.su2_plan(ctypes.byref(h), ctypes.byref(_desc(N=32, dtype=0, algo=2, flags=0x4))) == 2
     assert lib.su2_plan(ctypes.byref(h), ctypes.byref(_desc(N=512, dtype=0, algo=2, flags=0x4))) == 2
     assert lib.su2_plan(ctypes.byref(h), ctypes.byref(_desc(N=64, dtype=1, algo=1, flags=0x4))) == 2
+    # printed grid: complex64 only, and not together with the full-group grid
+    assert lib.su2_plan(ctypes.byref(h), ctypes.byref(_desc(N=16, dtype=1, algo=1, flags=0x8))) == 2
+    assert lib.su2_plan(ctypes.byref(h), ctypes.byref(_desc(N=64, dtype=0, algo=2, flags=0xC))) == 1
 
 
 def test_null_plan_calls(lib):
