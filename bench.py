@@ -214,8 +214,39 @@ def _time_ms(torch, stream, fn, steps=5, warmup=2):
     return a.elapsed_time(b) / steps
 
 
-def secondary_workloads(su2, I, torch, dev, stream):
+def secondary_workloads(su2, I, torch, dev, stream, peaks, fp32_peak):
     out = {}
+    gen0 = torch.Generator(device=dev)
+    gen0.manual_seed(6)
+    # other sampling grids (tensor-core contraction): stage 1 timed alone and in the forward
+    for key, N, B, kw, desc in (
+            ("full_group_n256_b32", 256, 32, {"full_group": True},
+             "full-group grid (psi over [-2 pi, 2 pi), 2N nodes), N=256, batch 32, complex64, seeded white noise"),
+            ("literal_grid_n256_b8", 256, 8, {"literal": True},
+             "printed grid (spacing 2 pi/(N-1), endpoint repeated), N=256, batch 8, complex64, seeded white noise")):
+        plan = su2.Plan(N=N, batch=B, dtype="c64", algo="tc_bf16x3", **kw)
+        x = torch.randn(plan.grid_elems, dtype=torch.complex64, device=dev, generator=gen0)
+        y = torch.empty(plan.coeff_elems, dtype=torch.complex64, device=dev)
+        ws = plan.workspace()
+        s1 = _time_ms(torch, stream, lambda: plan.forward_stage1(x, ws=ws, stream=stream), steps=5)
+        tot = _time_ms(torch, stream, lambda: plan.forward(x, out=y, ws=ws, stream=stream), steps=5)
+        plan.sync_status()
+        planes = 8 * (2 * N * N - 2 * N + 1) * N
+        r = {"workload": desc, "forward_ms": tot, "FFTs/s": B / tot * 1e3, "stage1_ms": s1}
+        if kw.get("literal"):
+            M = N - 1
+            flops = 8.0 * (M * M * N + M * N * N) * 2 * N * B        # two (N-1)-point DFT products per plane
+            r["stage1_roofline"] = {"bound": "alu", "kernel": "fft_fwd_literal", "achieved": flops / s1 / 1e9,
+                                    "peak": fp32_peak, "unit": "TFLOP/s", "frac": flops / s1 / 1e9 / fp32_peak}
+        else:
+            byts = (16.0 * N ** 3 + planes) * B                          # 2N^3 grid read + planes written
+            r["stage1_roofline"] = {"bound": "hbm", "kernel": "fft_fwd_two_phase (full group)",
+                                    "achieved": byts / s1 / 1e6, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                    "frac": byts / s1 / 1e6 / peaks["hbm_gbs"]}
+        out[key] = r
+        plan.close()
+        del x, y, ws
+        torch.cuda.empty_cache()
     # ragged batch: 512 functions, N uniform over {16, 32, 64, 128} (seed 3)
     rng = np.random.default_rng(3)
     Ns = I.draw_ragged_bandwidths(512, (16, 32, 64, 128), rng)
@@ -469,7 +500,7 @@ def main():
     if world == 1 and not args.no_extra and N == 256 and B == 64:
         del grid, outs, plans, plan, ws
         torch.cuda.empty_cache()
-        extra = secondary_workloads(su2, I, torch, dev, stream)
+        extra = secondary_workloads(su2, I, torch, dev, stream, peaks, fp32_peak)
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
