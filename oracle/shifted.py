@@ -17,10 +17,22 @@ These are the paper's identities for the m = n = 0 case, used as oracle pins
   epsilon_1; the composition rule lowers the subscript of every factor but the
   last (n_i - epsilon_i for i < k).  The two agree for k = 2 (the worked
   Example); for k >= 3 this module follows the composition rule.
+
+The end of Sec. 4 states that the same construction applies to the polynomials
+of the other matrix entries (m, n not both 0) through their own three-term
+recurrence.  ``wigner_shifted_AB`` and ``wigner_projection`` take that
+statement literally for d^l_{nm}: A_r^L, B_r^L are generated by the Wigner
+recurrence in r (step coefficients at degree L + r) from the same initial
+values, so d^{L+r} = A_r^L d^L + B_r^L d^{L-1}, and the depth-k expansion is
+the composition-rule form above.  ``forward_depth`` is the whole forward
+transform with stage 2 computed that way, the split of each shift r into k
+parts taken from the digits of r in base b (``digit_parts``), as in the GPU
+depth-k contraction.
 """
 from __future__ import annotations
 
 import itertools
+import math
 
 import numpy as np
 
@@ -113,3 +125,121 @@ def projection_printed(s: np.ndarray, L: int, parts, x: np.ndarray) -> float:
                 v = v * (Ai if eps[i - 1] == 0 else Bi)
             total += float(np.dot(svec[tau1], v))
     return total
+
+
+# ---------------------------------------------------------------------------
+# The (m, n) analogue: shifted polynomials of the Wigner-d recurrence
+# ---------------------------------------------------------------------------
+
+def _wigner_step(n2: int, m2: int, l: float):
+    """Coefficients (a, b, c) of d^{l+1} = a (x - b) d^l - c d^{l-1} for the pair
+    (n, m) = (n2/2, m2/2) (the Jacobi three-term recurrence in l)."""
+    n, m = n2 / 2.0, m2 / 2.0
+    if l == 0.0:
+        return 1.0, 0.0, 0.0
+    q1 = ((l + 1) ** 2 - n * n) * ((l + 1) ** 2 - m * m)
+    q0 = (l * l - n * n) * (l * l - m * m)
+    return ((l + 1) * (2 * l + 1) / math.sqrt(q1), n * m / (l * (l + 1)),
+            (l + 1) / l * math.sqrt(max(q0, 0.0)) / math.sqrt(q1))
+
+
+def wigner_shifted_AB(n2: int, m2: int, L2: int, rmax: int, x: np.ndarray):
+    """A_r^L(x), B_r^L(x), r = -1..rmax, of the pair (n, m) from degree L = L2/2:
+    d^{L+r}_{nm} = A_r^L d^L_{nm} + B_r^L d^{L-1}_{nm}.  Indexed r + 1."""
+    x = np.asarray(x, dtype=np.float64)
+    A = np.zeros((rmax + 2,) + x.shape)
+    B = np.zeros((rmax + 2,) + x.shape)
+    A[0], B[0] = 0.0, 1.0          # r = -1
+    A[1], B[1] = 1.0, 0.0          # r = 0
+    for r in range(0, rmax):
+        a, b, c = _wigner_step(n2, m2, L2 / 2.0 + r)
+        A[r + 2] = a * (x - b) * A[r + 1] - c * A[r]
+        B[r + 2] = a * (x - b) * B[r + 1] - c * B[r]
+    return A, B
+
+
+def _wAB(n2, m2, L2, r, x):
+    A, B = wigner_shifted_AB(n2, m2, L2, max(r, 0), x)
+    return A[r + 1], B[r + 1]
+
+
+def wigner_projection(s: np.ndarray, dL: np.ndarray, dLm1: np.ndarray, n2: int, m2: int, L2: int,
+                      parts, x: np.ndarray) -> float:
+    """<s, d^{L+r}_{nm}>, r = sum(parts), as the 2^k inner products of the
+    divide-and-conquer Theorem (composition-rule reading): s^L = s d^L,
+    s^{L-1} = s d^{L-1} given; each term is <s^{L or L-1}, V> with V the
+    Hadamard product of k shifted polynomials at levels L_0 = L,
+    L_i = L_{i-1} + n_i, orders n_i - eps_i (eps_k = 0)."""
+    k = len(parts)
+    svec = {"A": s * dL, "B": s * dLm1}
+    Ls = [L2]
+    for n in parts[:-1]:
+        Ls.append(Ls[-1] + 2 * n)
+    total = 0.0
+    for tau1 in ("A", "B"):
+        for eps in itertools.product((0, 1), repeat=k - 1):
+            e = list(eps) + [0]
+            v = np.ones_like(x, dtype=np.float64)
+            tau = tau1
+            for i in range(k):
+                Ai, Bi = _wAB(n2, m2, Ls[i], parts[i] - e[i], x)
+                v = v * (Ai if tau == "A" else Bi)
+                tau = "A" if e[i] == 0 else "B"
+            total = total + np.dot(svec[tau1], v)
+    return total
+
+
+def depth_base(R: int, k: int) -> int:
+    """Smallest base b >= 1 with b^k >= R + 1: every shift r <= R has k digits."""
+    b = 1
+    while b ** k < R + 1:
+        b += 1
+    return b
+
+
+def digit_parts(r: int, b: int, k: int):
+    """Parts n_i = d_i b^{k-i} of r = sum_i d_i b^{k-i} (digits of r in base b)."""
+    out = []
+    for i in range(k):
+        p = b ** (k - 1 - i)
+        out.append((r // p) * p)
+        r -= (r // p) * p
+    return out
+
+
+def forward_depth(f: np.ndarray, k: int, weights: str = "cc") -> np.ndarray:
+    """Forward transform with stage 2 by the depth-k divide-and-conquer projection.
+
+    Stage 1 as in ``transform.forward_separable``.  Per pair (n, m) with
+    mu = max(|n|, |m|): l = mu and mu + 1 directly; from the base L = mu + 1,
+    each l = L + r (r = 1..R) by ``wigner_projection`` with the parts of
+    ``digit_parts(r, depth_base(R, k), k)``.  Equal to the plain definition
+    up to rounding (pinned against it)."""
+    from . import basis, grid, quadrature, transform
+    N = f.shape[0]
+    al, be, ga = grid.alpha_nodes(N), grid.beta_nodes(N), grid.gamma_nodes(N)
+    w = quadrature.weights(N, weights)
+    pref = transform._prefactor(N, False)
+    x = np.cos(be)
+    out = np.zeros(grid.num_coeffs(N), dtype=np.complex128)
+    for sector in ("int", "half"):
+        idx = transform.sector_indices(N, sector)
+        jtop = transform._top_j(N, sector)
+        F2 = transform.torus_dft(f, idx, idx, al, ga)
+        for ni, n2 in enumerate(idx):
+            for mi, m2 in enumerate(idx):
+                j0, D = basis.wigner_d_column(n2, m2, be, jtop)
+                if D.shape[0] == 0:
+                    continue
+                s = w * F2[:, ni, mi]
+                vals = [np.dot(D[0], s)]
+                if D.shape[0] > 1:
+                    vals.append(np.dot(D[1], s))
+                R = D.shape[0] - 2
+                b = depth_base(R, k)
+                for r in range(1, R + 1):
+                    vals.append(wigner_projection(s, D[1], D[0], n2, m2, j0 + 2, digit_parts(r, b, k), x))
+                ph = pref * basis.i_pow((n2 - m2) // 2)
+                for i, v in enumerate(vals):
+                    out[grid.coeff_index(j0 + 2 * i, m2, n2)] = ph * v
+    return out
