@@ -189,6 +189,26 @@ su2_status su2_forward(su2_plan_t plan, const void* grid, void* coeffs, void* ws
 su2_status su2_forward_stage1(su2_plan_t plan, const void* grid, void* ws, void* cuda_stream);
 su2_status su2_forward_stage2(su2_plan_t plan, const void* ws, void* coeffs, void* cuda_stream);
 
+/* Stage 2 by the divide-and-conquer projection of Sec. 4 (Theorem
+ * "Divide-and-conquer" with the composition Proposition) at recursion depth
+ * k = depth, 1 <= depth <= 5.  Per pair (n, m): l = mu, mu + 1 directly; from
+ * the base L = mu + 1, every l = L + r is the sum of the Theorem's 2^k inner
+ * products <s^L or s^{L-1}, V>, V a Hadamard product of k shifted polynomials
+ * (for m, n != 0 those of the Wigner recurrence, the analogue the end of
+ * Sec. 4 states), the shift r split into its digits in base b, b the smallest
+ * base with b^k > R.  The result equals su2_forward_stage2's up to rounding;
+ * the cost grows as 2^k inner products per coefficient (Sec. 6, Proposition
+ * "Second Stage Complexity"; Theorem "optimal k" picks k = 1, which
+ * su2_forward_stage2 computes with one inner product per coefficient), so
+ * this entry point is for measuring that cost, not for speed.
+ *   ws:     workspace holding the stage-1 planes (su2_forward_stage1);
+ *   coeffs: output, layout as su2_forward.
+ * complex128 plans on the periodic grid only (FP64 arithmetic: the shifted
+ * polynomials and the seeds span more range than FP32 holds); other plans
+ * return SU2_ERR_UNSUPPORTED, depth outside 1..5 SU2_ERR_INVALID_ARG. */
+su2_status su2_forward_stage2_depth(su2_plan_t plan, int depth, const void* ws, void* coeffs,
+                                    void* cuda_stream);
+
 /* Synthesis: coeffs -> grid (Sec. 3 expansion with the (2l+1) factor). */
 su2_status su2_inverse(su2_plan_t plan, const void* coeffs, void* grid, void* ws,
                        void* cuda_stream);

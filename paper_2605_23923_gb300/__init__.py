@@ -138,6 +138,18 @@ class Plan:
                                                                       _stream_ptr(stream)))
         return out
 
+    def forward_stage2_depth(self, depth: int, out: torch.Tensor | None = None, ws: torch.Tensor | None = None,
+                             stream=None) -> torch.Tensor:
+        """Stage 2 by the depth-k divide-and-conquer projection (complex128 plans)."""
+        ws = self.workspace() if ws is None else ws
+        if out is None:
+            out = torch.empty(self.coeff_elems, dtype=self.torch_dtype, device=ws.device)
+        self._check_tensor(out, self.coeff_elems, "coeffs")
+        _abi.check("su2_forward_stage2_depth",
+                   self._lib.su2_forward_stage2_depth(self._h, int(depth), ws.data_ptr(), out.data_ptr(),
+                                                      _stream_ptr(stream)))
+        return out
+
     def inverse(self, coeffs: torch.Tensor, out: torch.Tensor | None = None, ws: torch.Tensor | None = None,
                 stream=None) -> torch.Tensor:
         self._check_tensor(coeffs, self.coeff_elems, "coeffs")

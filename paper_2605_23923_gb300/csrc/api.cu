@@ -685,6 +685,22 @@ su2_status su2_forward_stage2(su2_plan_t plan, const void* ws, void* coeffs, voi
     return SU2_OK;
 }
 
+su2_status su2_forward_stage2_depth(su2_plan_t plan, int depth, const void* ws, void* coeffs, void* stream) {
+    su2_status s = check_exec(plan, ws ? ws : coeffs, coeffs, ws);
+    if (s != SU2_OK) return s;
+    if (depth < 1 || depth > 5) return SU2_ERR_INVALID_ARG;
+    if (plan->dtype != SU2_C128 || (plan->flags & (SU2_FLAG_FULL_GROUP | SU2_FLAG_LITERAL_GRID)))
+        return SU2_ERR_UNSUPPORTED;
+    DeviceGuard g(plan->device);
+    if (!g.ok) return SU2_ERR_CUDA;
+    for (auto& kv : plan->bands) {
+        const su2::BandArgs a = band_args(plan, kv.second);
+        const cudaError_t e = su2::launch_contract_forward_depth(a, depth, ws, coeffs, (cudaStream_t)stream);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    return SU2_OK;
+}
+
 static su2_status run_transpose(su2_plan_t plan, su2::TransposeMode mode, const void* coeffs, void* grid,
                                 void* ws, void* stream) {
     su2_status s = check_exec(plan, coeffs, grid, ws);

@@ -33,6 +33,10 @@ cudaError_t launch_fft_inverse(const BandArgs& a, bool fp64, const void* ws, voi
 // transposed contraction (synthesis with weight 2l+1, or adjoint with weight
 // w_k/(2N^2)).
 cudaError_t launch_contract_forward(const BandArgs& a, bool fp64, const void* ws, void* coeffs, cudaStream_t st);
+// The same contraction by the depth-k divide-and-conquer projection (complex128
+// planes, N <= 256, depth 1..5).
+cudaError_t launch_contract_forward_depth(const BandArgs& a, int depth, const void* ws, void* coeffs,
+                                          cudaStream_t st);
 enum class TransposeMode { Synthesis = 0, Adjoint = 1 };
 cudaError_t launch_contract_transpose(const BandArgs& a, bool fp64, TransposeMode mode, const void* coeffs,
                                       void* ws, cudaStream_t st);
