@@ -214,6 +214,27 @@ def _time_ms(torch, stream, fn, steps=5, warmup=2):
     return a.elapsed_time(b) / steps
 
 
+def depth_op_counts(N, k):
+    """Per function, for the depth-k stage 2 at bandwidth N: the inner-product
+    multiply-adds it executes (2^k per node for every coefficient l >= mu + 2,
+    one for l = mu, mu + 1) and the Sec. 6 cost model 2^k k N per coefficient."""
+    macs = paper = 0
+    for s in (0, 1):
+        jtop = N - 2 + s
+        for mi in range(N):
+            for ni in range(N):
+                if s == 0 and (mi == 0 or ni == 0):
+                    continue
+                mu2 = max(abs(2 * (mi - N // 2) + s), abs(2 * (ni - N // 2) + s))
+                if mu2 > jtop:
+                    continue
+                rows = (jtop - mu2) // 2 + 1
+                direct = min(rows, 2)
+                macs += N * (direct + (2 ** k) * (rows - direct))
+                paper += (2 ** k) * k * N * rows
+    return {"macs": macs, "paper": paper}
+
+
 def secondary_workloads(su2, I, torch, dev, stream, peaks, fp32_peak):
     out = {}
     gen0 = torch.Generator(device=dev)
@@ -247,6 +268,28 @@ def secondary_workloads(su2, I, torch, dev, stream, peaks, fp32_peak):
         plan.close()
         del x, y, ws
         torch.cuda.empty_cache()
+    # depth-k divide-and-conquer stage 2 (Sec. 4 Theorem) against the fused recurrence
+    N, B = 128, 16
+    plan = su2.Plan(N=N, batch=B, dtype="c128", algo="fp64")
+    x = torch.randn(plan.grid_elems, dtype=torch.complex128, device=dev, generator=gen0)
+    y = torch.empty(plan.coeff_elems, dtype=torch.complex128, device=dev)
+    ws = plan.workspace()
+    plan.forward_stage1(x, ws=ws, stream=stream)
+    rec = _time_ms(torch, stream, lambda: plan.forward_stage2(out=y, ws=ws, stream=stream), steps=3, warmup=1)
+    dk = {"workload": "N=128, batch 16, complex128 (FP64), seeded white noise; stage 2 only, planes resident",
+          "recurrence_contraction_ms": rec, "by_depth": {}}
+    for k in (1, 2, 3, 4, 5):
+        ms = _time_ms(torch, stream, lambda: plan.forward_stage2_depth(k, out=y, ws=ws, stream=stream),
+                      steps=2, warmup=1)
+        ops = depth_op_counts(N, k)
+        dk["by_depth"][str(k)] = {"ms": ms, "ms_over_recurrence": ms / rec,
+                                  "inner_product_macs_per_function": ops["macs"],
+                                  "paper_model_ops_per_function": ops["paper"]}
+    plan.sync_status()
+    out["depth_k_stage2_n128_b16"] = dk
+    plan.close()
+    del x, y, ws
+    torch.cuda.empty_cache()
     # ragged batch: 512 functions, N uniform over {16, 32, 64, 128} (seed 3)
     rng = np.random.default_rng(3)
     Ns = I.draw_ragged_bandwidths(512, (16, 32, 64, 128), rng)
