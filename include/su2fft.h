@@ -240,6 +240,33 @@ su2_status su2_forward_noalloc(su2_plan_t plan, const void* grid, void* coeffs, 
 /* Synchronises the stream and reports any latched device-side error; clears it. */
 su2_status su2_sync_status(su2_plan_t plan, void* cuda_stream);
 
+/* Forward transform of a batch held in host memory (a library service; the
+ * transform is su2_forward's).  The grids are uploaded in chunks of about
+ * 1 GiB on a plan-owned copy stream while stage 1 runs on the chunks already
+ * resident; stage 2 then runs per bandwidth group over all its functions and
+ * each group's coefficients are downloaded on a second copy stream; finally
+ * `cuda_stream` waits for the downloads, so host_coeffs is complete once that
+ * stream has passed this call (e.g. after cudaStreamSynchronize).
+ *   host_grid:   host memory, su2_grid_elems elements (page-locked memory is
+ *                needed for the copies to overlap the kernels); it must stay
+ *                unchanged until the stream has passed this call.
+ *   host_coeffs: host memory, su2_coeff_elems elements (page-locked likewise).
+ *   dev_grid:    device memory, su2_grid_elems elements, used as the staging
+ *                buffer of this call: the uploads start as soon as this plan's
+ *                previous su2_forward_pipelined call has finished its stage 1,
+ *                without waiting for other work queued on cuda_stream, so it
+ *                must not be in use by such work.
+ *   dev_coeffs:  device memory, su2_coeff_elems elements (device copy of the
+ *                result, left in place).
+ *   ws:          workspace as for su2_forward.
+ * Consecutive calls on one plan must use the same stream (they then overlap:
+ * the next call's uploads run during this call's stage 2 and downloads).
+ * The first call creates the plan's two copy streams and four events.  Not
+ * recorded into the plan's CUDA graph.  Errors as su2_forward; a null host
+ * pointer is SU2_ERR_INVALID_ARG. */
+su2_status su2_forward_pipelined(su2_plan_t plan, const void* host_grid, void* host_coeffs, void* dev_grid,
+                                 void* dev_coeffs, void* ws, void* cuda_stream);
+
 su2_status su2_destroy(su2_plan_t plan);
 
 const char* su2_status_string(su2_status s);

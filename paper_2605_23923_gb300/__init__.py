@@ -138,6 +138,32 @@ class Plan:
                                                                       _stream_ptr(stream)))
         return out
 
+    def forward_pipelined(self, host_grid: torch.Tensor, host_out: torch.Tensor | None = None,
+                          dev_grid: torch.Tensor | None = None, dev_out: torch.Tensor | None = None,
+                          ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Forward transform of grids in host memory (pinned for overlap) into host
+        coefficients, streamed through the device; returns host_out (complete once
+        the stream has passed the call)."""
+        if host_grid.device.type != "cpu" or not host_grid.is_contiguous() or host_grid.dtype != self.torch_dtype \
+                or host_grid.numel() != self.grid_elems:
+            raise ValueError("host_grid: contiguous CPU tensor of the plan's dtype and grid_elems elements")
+        dev = torch.device(f"cuda:{self.device}")
+        if host_out is None:
+            host_out = torch.empty(self.coeff_elems, dtype=self.torch_dtype, pin_memory=True)
+        if host_out.device.type != "cpu" or not host_out.is_contiguous() or host_out.dtype != self.torch_dtype \
+                or host_out.numel() != self.coeff_elems:
+            raise ValueError("host_out: contiguous CPU tensor of the plan's dtype and coeff_elems elements")
+        dev_grid = torch.empty(self.grid_elems, dtype=self.torch_dtype, device=dev) if dev_grid is None else dev_grid
+        dev_out = torch.empty(self.coeff_elems, dtype=self.torch_dtype, device=dev) if dev_out is None else dev_out
+        self._check_tensor(dev_grid, self.grid_elems, "dev_grid")
+        self._check_tensor(dev_out, self.coeff_elems, "dev_out")
+        ws = self.workspace() if ws is None else ws
+        _abi.check("su2_forward_pipelined",
+                   self._lib.su2_forward_pipelined(self._h, host_grid.data_ptr(), host_out.data_ptr(),
+                                                   dev_grid.data_ptr(), dev_out.data_ptr(), ws.data_ptr(),
+                                                   _stream_ptr(stream)))
+        return host_out
+
     def forward_stage2_depth(self, depth: int, out: torch.Tensor | None = None, ws: torch.Tensor | None = None,
                              stream=None) -> torch.Tensor:
         """Stage 2 by the depth-k divide-and-conquer projection (complex128 plans)."""

@@ -111,6 +111,9 @@ struct su2_plan_s {
     std::vector<cudaEvent_t> ev_join;
     cudaEvent_t ev_fork = nullptr;
     cudaStream_t cap_stream = nullptr;
+    // host-resident batches (su2_forward_pipelined): upload / download streams and hand-off events
+    cudaStream_t pipe_up = nullptr, pipe_down = nullptr;
+    cudaEvent_t ev_up = nullptr, ev_s1done = nullptr, ev_s2 = nullptr, ev_down = nullptr;
     struct GraphEntry {
         const void* grid;
         void* coeffs;
@@ -138,6 +141,10 @@ struct su2_plan_s {
         if (ev_fork) cudaEventDestroy(ev_fork);
         ev_fork = nullptr;
         if (cap_stream) cudaStreamDestroy(cap_stream);
+        for (cudaStream_t* s : {&pipe_up, &pipe_down})
+            if (*s) { cudaStreamDestroy(*s); *s = nullptr; }
+        for (cudaEvent_t* ev : {&ev_up, &ev_s1done, &ev_s2, &ev_down})
+            if (*ev) { cudaEventDestroy(*ev); *ev = nullptr; }
         cap_stream = nullptr;
         for (void* p : allocs) cudaFree(p);
         allocs.clear();
@@ -303,6 +310,81 @@ cudaError_t enqueue_forward(su2_plan_s* P, const void* grid, void* coeffs, void*
         ++i;
     }
     return cudaSuccess;
+}
+
+// Band arguments restricted to functions [f0, f0 + cnt) of the band (contiguous
+// grids and planes, so the group offsets are those of function f0).
+su2::BandArgs sub_band_args(const su2_plan_s* P, const Band& b, int f0, int cnt) {
+    su2::BandArgs a = band_args(P, b);
+    a.nfunc = cnt;
+    a.fidx = b.d_fidx + f0;
+    a.grid_group_off = P->grid_off[b.fids[f0]];
+    a.ws_group_off = P->ws_off[b.fids[f0]];
+    return a;
+}
+
+// Host-resident batch: uploads in chunks of about 1 GiB of grids on pipe_up,
+// stage 1 of each chunk on `st` as soon as it has landed, then stage 2 per
+// group and the download of its coefficients on pipe_down; `st` finally waits
+// for the downloads.  The next call's uploads wait only for this call's
+// stage 1 (the last reader of dev_grid), so they overlap this call's stage 2
+// and downloads.
+cudaError_t forward_pipelined(su2_plan_s* P, const void* hgrid, void* hcoeffs, void* dgrid, void* dcoeffs,
+                              void* ws, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    if (!P->pipe_up) {
+        if ((e = cudaStreamCreateWithFlags(&P->pipe_up, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        if ((e = cudaStreamCreateWithFlags(&P->pipe_down, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        for (cudaEvent_t* ev : {&P->ev_up, &P->ev_s1done, &P->ev_s2, &P->ev_down})
+            if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess) return e;
+    }
+    const bool fp64 = P->dtype == SU2_C128;
+    const size_t esz = fp64 ? 16 : 8;
+    const char* hg = static_cast<const char*>(hgrid);
+    char* dg = static_cast<char*>(dgrid);
+    if ((e = cudaStreamWaitEvent(P->pipe_up, P->ev_s1done, 0)) != cudaSuccess) return e;
+    for (auto& kv : P->bands) {
+        const Band& b = kv.second;
+        const size_t N = (size_t)b.N;
+        const size_t gbytes = (b.full_group ? 2 : 1) * N * N * N * esz;     // one grid
+        const int nf = (int)b.fids.size();
+        const int per = (int)std::max<size_t>(1, ((size_t)1 << 30) / gbytes);
+        for (int f0 = 0; f0 < nf; f0 += per) {
+            const int cnt = std::min(per, nf - f0);
+            const size_t off = P->grid_off[b.fids[f0]] * esz;                // grids of a group are contiguous
+            if ((e = cudaMemcpyAsync(dg + off, hg + off, (size_t)cnt * gbytes, cudaMemcpyHostToDevice,
+                                     P->pipe_up)) != cudaSuccess)
+                return e;
+            if ((e = cudaEventRecord(P->ev_up, P->pipe_up)) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(st, P->ev_up, 0)) != cudaSuccess) return e;
+            if ((e = su2::launch_fft_forward(sub_band_args(P, b, f0, cnt), fp64, dgrid, ws, st)) != cudaSuccess)
+                return e;
+        }
+    }
+    if ((e = cudaEventRecord(P->ev_s1done, st)) != cudaSuccess) return e;
+    const char* dc = static_cast<const char*>(dcoeffs);
+    char* hc = static_cast<char*>(hcoeffs);
+    for (auto& kv : P->bands) {
+        const Band& b = kv.second;
+        const su2::BandArgs a = band_args(P, b);
+        e = b.tc ? su2::launch_contract_forward_tc(a, ws, dcoeffs, st)
+                 : su2::launch_contract_forward(a, fp64, ws, dcoeffs, st);
+        if (e != cudaSuccess) return e;
+        if ((e = cudaEventRecord(P->ev_s2, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(P->pipe_down, P->ev_s2, 0)) != cudaSuccess) return e;
+        const size_t csz = ncoef(b.N) * esz;
+        for (size_t i = 0; i < b.fids.size();) {           // runs of adjacent coefficient blocks
+            size_t j = i + 1;
+            while (j < b.fids.size() && P->coeff_off[b.fids[j]] == P->coeff_off[b.fids[j - 1]] + ncoef(b.N)) ++j;
+            const size_t off = P->coeff_off[b.fids[i]] * esz;
+            if ((e = cudaMemcpyAsync(hc + off, dc + off, (j - i) * csz, cudaMemcpyDeviceToHost, P->pipe_down)) !=
+                cudaSuccess)
+                return e;
+            i = j;
+        }
+    }
+    if ((e = cudaEventRecord(P->ev_down, P->pipe_down)) != cudaSuccess) return e;
+    return cudaStreamWaitEvent(st, P->ev_down, 0);
 }
 
 // The forward transform as a CUDA graph recorded once per pointer triple.
@@ -654,6 +736,16 @@ su2_status su2_forward(su2_plan_t plan, const void* grid, void* coeffs, void* ws
     const cudaError_t e = (plan->flags & SU2_FLAG_CUDA_GRAPH) ? forward_graph(plan, grid, coeffs, ws, st)
                                                              : enqueue_forward(plan, grid, coeffs, ws, st);
     return from_cuda(e);
+}
+
+su2_status su2_forward_pipelined(su2_plan_t plan, const void* host_grid, void* host_coeffs, void* dev_grid,
+                                 void* dev_coeffs, void* ws, void* stream) {
+    su2_status s = check_exec(plan, dev_grid, dev_coeffs, ws);
+    if (s != SU2_OK) return s;
+    if (!host_grid || !host_coeffs) return SU2_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    if (!g.ok) return SU2_ERR_CUDA;
+    return from_cuda(forward_pipelined(plan, host_grid, host_coeffs, dev_grid, dev_coeffs, ws, (cudaStream_t)stream));
 }
 
 su2_status su2_forward_stage1(su2_plan_t plan, const void* grid, void* ws, void* stream) {
