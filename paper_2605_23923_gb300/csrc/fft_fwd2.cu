@@ -61,7 +61,7 @@ struct Cfg {
     static constexpr int NS = 2;                        // ring slots
     static constexpr int BOXR = N < 256 ? N : 256;      // rows per TMA box (at most 256)
     static constexpr size_t smem_bytes() {
-        return (size_t)NS * SLOTP * 8 + (size_t)YP * 8 + (size_t)N * 8 * 2 + (size_t)N * 4 + 2 * NS * 8 + NS * 4;
+        return (size_t)NS * SLOTP * 8 + (size_t)YP * 8 + (size_t)N * 8 * 3 + (size_t)N * 4 + 2 * NS * 8 + NS * 4;
     }
     static constexpr int BLOCKS_PER_SM =
         FULL ? (N <= 128 ? 2 : 1) : ((N <= 64) ? 4 : (N <= 128) ? 3 : (N <= 256 ? 2 : 1));
@@ -152,7 +152,8 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
     float2* Y = S + NS * P::SLOTP;                             // sector-1 columns of an A item
     float2* om = Y + P::YP;                                    // exp(+2 pi i t/N)
     float2* tw = om + N;                                       // exp(+i pi t/N)
-    float* wk = reinterpret_cast<float*>(tw + N);
+    float2* omq = tw + N;                                      // [q][ia] = om[ia * q] (B items: lanes vary ia)
+    float* wk = reinterpret_cast<float*>(omq + N);
     uint64_t* full = reinterpret_cast<uint64_t*>(wk + N);      // [NS]
     uint64_t* empty = full + NS;                               // [NS]
     int* slot_item = reinterpret_cast<int*>(empty + NS);       // [NS] item held by a slot (-1: end)
@@ -167,6 +168,7 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
 
     for (int t = tid; t < N; t += blockDim.x) {
         om[t] = a.om32[t];
+        omq[t] = a.om32[(t % R1) * (t / R1)];                  // t = q * R1 + ia, ia * q < N
         tw[t] = a.twist32[t];
         wk[t] = a.w32[t];
     }
@@ -236,10 +238,13 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
                                      &full[b]);
                 }
             } else if (lane == 0) {
-                // B item: the compute threads read the rows from L2 themselves; the
-                // slot only serves as their transpose buffer.  Signal the dependency.
+                // B item: its W intermediate rows are contiguous in the ring (they stay in
+                // L2); one bulk copy brings them into the slot once the plane's A items
+                // are done, so the compute warps never wait on L2 latency themselves.
                 wait_counter(&doneA[r], (use + 1) * P::NA, a.err);
-                mbar_arrive_cta(&full[b]);
+                fence_proxy_async_global();          // the acquire above orders the copy's reads
+                mbar_arrive_expect_tx(&full[b], (uint32_t)(SLOT * 8));
+                bulk_g2s(dst, ring + ((size_t)(r * 2 + it.s) * N + it.pb * W) * N, (uint32_t)(SLOT * 8), &full[b]);
             }
             __syncwarp();
         }
@@ -314,21 +319,22 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
                 atomicAdd(&doneA[r], 1u);
             }
         } else {
-            // Pass a: R2-point DFTs over j2 = ia + R1*q of row pl, read straight from
-            // the intermediate in L2; written into the slot with the odd row pitch N + 1.
+            // Pass a: R2-point DFTs over j2 = ia + R1*q of row pl, from the rows the
+            // producer copied into the slot (pitch N); written back with the odd row
+            // pitch N + 1.
             const float2* rows = ring + ((size_t)(r * 2 + it.s) * N + it.pb * W) * N;
             {
                 const int ia = tid % R1, pl = tid / R1;            // W * R1 == CT
                 float2 v[R2];
 #pragma unroll
-                for (int q = 0; q < R2; ++q) v[q] = __ldcs(rows + pl * N + ia + R1 * q);
+                for (int q = 0; q < R2; ++q) v[q] = X[pl * N + ia + R1 * q];
                 if (it.s) {
 #pragma unroll
                     for (int q = 0; q < R2; ++q) v[q] = cmul(v[q], tw[ia + R1 * q]);
                 }
                 dft_reg<R2, 1, float>(v);
 #pragma unroll
-                for (int q = 1; q < R2; ++q) v[q] = cmul(v[q], om[ia * q]);
+                for (int q = 1; q < R2; ++q) v[q] = cmul(v[q], omq[q * R1 + ia]);
                 named_sync(1, CT);        // every load of the item has been consumed
 #pragma unroll
                 for (int q = 0; q < R2; ++q) X[pl * P::PB + ia + R1 * q] = v[q];   // odd pitch: no conflicts
