@@ -269,8 +269,11 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
         }
     } else if ((warp >= W_CONV && warp < W_CONV + 4) || warp == W_CONV2 || warp == W_CONV2 + 1) {
         // ------------------------------------------------------------------ F2 -> A (bf16 hi/lo)
-        // Item = (function b, node pair kp, pair p): two staged values (nodes 2kp,
-        // 2kp+1) -> one bf16x2 word per row (re: 2b, im: 2b+1) for hi and lo.
+        // Item = (function b, node group t, pair p): four staged values (nodes t,
+        // t + 4, t + 8, t + 12 at K positions 4t .. 4t + 3 of the chunk) -> two
+        // bf16x2 words (8 bytes) per row (re: 2b, im: 2b+1) for hi and lo.  With this
+        // K order 16 lanes read 16 consecutive staged values (no bank conflicts) and
+        // the stores are 8 bytes; the generators write the d-values in the same order.
         const int cw = (warp < W_CONV + 4) ? warp - W_CONV : 4 + (warp - W_CONV2);
         const int ct = cw * 32 + lane;                     // 0 .. 191
         uint32_t g = 0;
@@ -285,18 +288,21 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
                 if (u > 0) mbar_wait_bounded(&bar_opfree[st], (u - 1) & 1, a.err);
                 const float2* stg = reinterpret_cast<const float2*>(smem + OFF_STG + st * STAGE_BYTES);
                 unsigned char* Ab = smem + OFF_A + st * A_BYTES;
-                for (int i = ct; i < BM * (KC / 2) * NP; i += 32 * N_CONV) {
-                    const int p = i & 3, kp = (i >> 2) & 7, b = i >> 5;
-                    const float2 v0 = stg[(b * KC + 2 * kp) * NP + p];
-                    const float2 v1 = stg[(b * KC + 2 * kp + 1) * NP + p];
-                    uint32_t hr, lr, hi_, li;
-                    split2(v0.x, v1.x, hr, lr);
-                    split2(v0.y, v1.y, hi_, li);
-                    const int ore = a_off(2 * b, 2 * kp), oim = a_off(2 * b + 1, 2 * kp);
-                    *reinterpret_cast<uint32_t*>(Ab + p * OPA + ore) = hr;
-                    *reinterpret_cast<uint32_t*>(Ab + p * OPA + oim) = hi_;
-                    *reinterpret_cast<uint32_t*>(Ab + (NP + p) * OPA + ore) = lr;
-                    *reinterpret_cast<uint32_t*>(Ab + (NP + p) * OPA + oim) = li;
+                for (int i = ct; i < BM * (KC / 4) * NP; i += 32 * N_CONV) {
+                    const int p = i & 3, t = (i >> 2) & 3, b = i >> 4;
+                    float2 v[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) v[q] = stg[(b * KC + t + 4 * q) * NP + p];
+                    uint2 hr, lr, hi_, li;
+                    split2(v[0].x, v[1].x, hr.x, lr.x);
+                    split2(v[2].x, v[3].x, hr.y, lr.y);
+                    split2(v[0].y, v[1].y, hi_.x, li.x);
+                    split2(v[2].y, v[3].y, hi_.y, li.y);
+                    const int ore = a_off(2 * b, 4 * t), oim = a_off(2 * b + 1, 4 * t);
+                    *reinterpret_cast<uint2*>(Ab + p * OPA + ore) = hr;
+                    *reinterpret_cast<uint2*>(Ab + p * OPA + oim) = hi_;
+                    *reinterpret_cast<uint2*>(Ab + (NP + p) * OPA + ore) = lr;
+                    *reinterpret_cast<uint2*>(Ab + (NP + p) * OPA + oim) = li;
                 }
                 fence_proxy_async_smem();
                 __syncwarp();
@@ -308,7 +314,8 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
         }
     } else if (warp >= W_GEN && warp < W_GEN + 4) {
         // ------------------------------------------------------------------ recurrence -> B (bf16 hi/lo)
-        // Thread (p, kk) runs the chain of pair p at node c*KC + kk for the chunks of
+        // Thread (p, kk) runs the chain of pair p at node c*KC + kk/4 + 4*(kk%4) (K
+        // position kk, the order the converters use) for the chunks of
         // its group's stage.  Seeds in FP32 from the split logarithms (exact
         // products and sums; only the pair's factorial ratio K is FP64, once per
         // tile).  Range extension: value = cur * 2^(-120 E); while E > 0 the value is
@@ -345,7 +352,7 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
                 if (u > 0) mbar_wait_bounded(&bar_opfree[st], (u - 1) & 1, a.err);
                 unsigned char* Bh = smem + OFF_B + st * B_BYTES + p * OPB + (kk >> 3) * LBO_B + (kk & 7) * 16;
                 unsigned char* Bl = Bh + NP * OPB;
-                const int k = c * KC + kk;
+                const int k = c * KC + ((kk >> 2) | ((kk & 3) << 2));   // node at K position kk
                 // seed
                 int E;
                 float cur = seed_value32(q, t_seed[k], k, N, E);
