@@ -48,6 +48,38 @@ PROFILED_TRAFFIC = {
 }
 
 
+# ---------------------------------------------------------------------------
+# Multi-rank host logic (one process per GPU under torchrun; replicas, no
+# collective on the data path): environment, per-rank seeds, the max over
+# ranks of a time, and the whole-job throughput.
+# ---------------------------------------------------------------------------
+def rank_env():
+    """(world size, rank, local rank) from the torchrun environment."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def rank_seed(rank):
+    """Seed of a rank's coefficients: 2 on rank 0, 2 + 1000 r on rank r."""
+    return 2 + 1000 * rank
+
+
+def max_over_ranks(x, world, device):
+    """The largest x over all ranks (every rank gets it); x itself when alone."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world, units_per_rank, steps, elapsed_ms):
+    """Units processed by all ranks per second, timed by the slowest rank."""
+    return world * units_per_rank * steps / (elapsed_ms / 1e3)
+
+
 def profiled_traffic(kernel, N, B):
     import hashlib
     ent = PROFILED_TRAFFIC.get(kernel)
@@ -173,7 +205,7 @@ def cpu_baseline_for(f64grid):
 
 def run_reference(args):
     """--impl reference: the FP64 oracle on the host cores."""
-    rank = int(os.environ.get("RANK", "0"))
+    _, rank, _ = rank_env()
     if rank != 0:
         return
     import su2inputs as I
@@ -355,9 +387,7 @@ def main():
     import su2inputs as I
     from paper_2605_23923_gb300 import build
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -384,7 +414,7 @@ def main():
 
     # ---- inputs: seeded coefficients -> grids by the library's synthesis
     C = num_coeffs(N)
-    rng = np.random.default_rng(2 + 1000 * rank)
+    rng = np.random.default_rng(rank_seed(rank))
     coeffs = torch.empty(B * C, dtype=torch.complex64, device=dev)
     for b in range(B):
         c = I.draw_coeffs(N, rng, "inv1").astype(np.complex64)
@@ -435,11 +465,7 @@ def main():
         if world > 1:
             dist.barrier()
         pl.sync_status()
-        el = t_start.elapsed_time(t_end)
-        if world > 1:
-            t = torch.tensor([el], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(t_start.elapsed_time(t_end), world, dev)
         return {"elapsed_ms": el, "st1": [e[0].elapsed_time(e[1]) for e in evs],
                 "st2": [e[1].elapsed_time(e[2]) for e in evs], "clocks": clk}
 
@@ -447,7 +473,7 @@ def main():
     elapsed_ms = res[algo]["elapsed_ms"]
     st1, st2, clk = res[algo]["st1"], res[algo]["st2"], res[algo]["clocks"]
     ms_per_step = elapsed_ms / args.steps
-    value = world * B * args.steps / (elapsed_ms / 1e3)
+    value = whole_job_value(world, B, args.steps, elapsed_ms)
     path_diff = None
     if len(algos) > 1:
         a0, a1 = outs[algos[0]], outs[algos[1]]
@@ -477,12 +503,8 @@ def main():
             e2e_step()
         b_.record(stream)
         torch.cuda.synchronize()
-        ems = a.elapsed_time(b_)
-        if world > 1:
-            t = torch.tensor([ems], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": world * B * args.e2e_steps / (ems / 1e3), "unit": UNIT,
+        ems = max_over_ranks(a.elapsed_time(b_), world, dev)
+        e2e = {"value": whole_job_value(world, B, args.e2e_steps, ems), "unit": UNIT,
                "h2d_bytes_per_step": host_grid.numel() * 8, "d2h_bytes_per_step": host_out.numel() * 8,
                "steps": args.e2e_steps}
         del host_grid, host_out, dgrid
@@ -507,7 +529,7 @@ def main():
         fft_gbs = fft_bytes / s1 / 1e9
         out = {
             "ms_per_step": r["elapsed_ms"] / args.steps,
-            "value": world * B * args.steps / (r["elapsed_ms"] / 1e3),
+            "value": whole_job_value(world, B, args.steps, r["elapsed_ms"]),
             "stage1_fft": {"ms": s1 * 1e3, "GB/s": fft_gbs, "bound": "hbm", "frac": fft_gbs / peaks["hbm_gbs"],
                            "alg_bytes": fft_bytes},
             "stage2_contraction": {"ms": s2 * 1e3, "algo": al, "alg_flops": contr_flops,
