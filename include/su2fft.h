@@ -240,6 +240,17 @@ su2_status su2_forward_noalloc(su2_plan_t plan, const void* grid, void* coeffs, 
 /* Synchronises the stream and reports any latched device-side error; clears it. */
 su2_status su2_sync_status(su2_plan_t plan, void* cuda_stream);
 
+/* Self-test of the device-side bounded waits (a library service, no
+ * counterpart in the paper).  Enqueues on cuda_stream one small kernel that
+ * waits, with the same bounded helpers the transform kernels use, for an event
+ * that never happens: kind 0 a counter in the plan's memory that nothing
+ * increments, kind 1 an mbarrier phase that nothing arrives on.  After about a
+ * second (2e9 SM cycles) the wait gives up, latches the plan's error word and
+ * the kernel returns, so the next su2_sync_status on that stream returns
+ * SU2_ERR_TIMEOUT (and clears the word) and the context stays usable.
+ * kind outside {0, 1}: SU2_ERR_INVALID_ARG. */
+su2_status su2_selftest_bounded_wait(su2_plan_t plan, int kind, void* cuda_stream);
+
 /* Forward transform of a batch held in host memory (a library service; the
  * transform is su2_forward's).  The grids are uploaded in chunks of about
  * 1 GiB on a plan-owned copy stream while stage 1 runs on the chunks already

@@ -198,6 +198,12 @@ class Plan:
                                                           ws.data_ptr(), _stream_ptr(stream)))
         return out
 
+    def selftest_bounded_wait(self, kind: int, stream=None):
+        """Enqueue a kernel whose bounded wait never completes (0: counter,
+        1: mbarrier); the next sync_status raises SU2Error with SU2_ERR_TIMEOUT."""
+        _abi.check("su2_selftest_bounded_wait",
+                   self._lib.su2_selftest_bounded_wait(self._h, int(kind), _stream_ptr(stream)))
+
     def sync_status(self, stream=None):
         _abi.check("su2_sync_status", self._lib.su2_sync_status(self._h, _stream_ptr(stream)))
 

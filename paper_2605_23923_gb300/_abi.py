@@ -61,6 +61,7 @@ SIGNATURES = [
     ("su2_forward_stage1", ctypes.c_int, [ctypes.c_void_p] * 4),
     ("su2_forward_stage2", ctypes.c_int, [ctypes.c_void_p] * 4),
     ("su2_forward_pipelined", ctypes.c_int, [ctypes.c_void_p] * 7),
+    ("su2_selftest_bounded_wait", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     ("su2_forward_stage2_depth", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 3),
     ("su2_forward_noalloc", ctypes.c_int, [ctypes.c_void_p] * 4),
     ("su2_inverse", ctypes.c_int, [ctypes.c_void_p] * 5),

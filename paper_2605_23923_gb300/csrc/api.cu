@@ -659,8 +659,8 @@ su2_status su2_plan(su2_plan_t* out, const su2_plan_desc* desc) {
     if (e == cudaSuccess) e = P->upload(&P->d_ws_off, P->ws_off.data(), P->B);
     if (e == cudaSuccess) e = P->upload(&P->d_lf2, lf2.data(), lf2.size());
     if (e == cudaSuccess) {
-        const int zero = 0;
-        e = P->upload(&P->d_err, &zero, 1);
+        const int zero[2] = {0, 0};      // error word; a word nothing ever writes (self-test)
+        e = P->upload(&P->d_err, zero, 2);
     }
     for (auto& kv : P->bands) {
         if (e != cudaSuccess) break;
@@ -835,6 +835,14 @@ su2_status su2_sync_status(su2_plan_t plan, void* stream) {
         return SU2_ERR_TIMEOUT;
     }
     return SU2_OK;
+}
+
+su2_status su2_selftest_bounded_wait(su2_plan_t plan, int kind, void* stream) {
+    if (!plan || (kind != 0 && kind != 1)) return SU2_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    if (!g.ok) return SU2_ERR_CUDA;
+    const unsigned* never = reinterpret_cast<const unsigned*>(plan->d_err + 1);
+    return from_cuda(su2::launch_bounded_wait_selftest(never, plan->d_err, kind, (cudaStream_t)stream));
 }
 
 su2_status su2_destroy(su2_plan_t plan) {

@@ -248,10 +248,28 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
-// Order this thread's earlier (acquired) view of global memory before its
-// later async-proxy (bulk copy) reads of global memory.
-__device__ __forceinline__ void fence_proxy_async_global() {
-    asm volatile("fence.proxy.async.global;" ::: "memory");
+// Acquire load of a counter that other CTAs increment (each after a
+// __threadfence and an atomicAdd).
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+// Spin until *ctr >= target (wrap-safe comparison), bounded like the mbarrier
+// waits: after 2e9 SM cycles (about a second) latch the error word and return.
+// Once any wait of the launch has timed out (error word set) the others return
+// at once, so a broken dependency costs one timeout, not one per item.
+__device__ __forceinline__ void wait_counter_bounded(const unsigned* ctr, unsigned target, int* err) {
+    if ((int)(ld_acquire_gpu(ctr) - target) >= 0) return;
+    const long long t0 = clock64();
+    while ((int)(ld_acquire_gpu(ctr) - target) < 0) {
+        if (*(volatile int*)err != 0) return;
+        __nanosleep(64);
+        if (clock64() - t0 > 2000000000LL) {
+            atomicExch(err, 1);
+            return;
+        }
+    }
 }
 // 1-D bulk copy global -> shared (this CTA), completion counted on `bar`.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {

@@ -83,11 +83,6 @@ __device__ __forceinline__ uint64_t policy_evict_first() {
 __device__ __forceinline__ void mbar_arrive_cta(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
 __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
@@ -96,21 +91,6 @@ __device__ __forceinline__ void discard_l2_line(const void* p) {
 }
 __device__ __forceinline__ void named_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 
-// Spin until *ctr >= target (wrap-safe); bounded like the mbarrier waits.  Once
-// any wait of the launch has timed out (error word set) the others return at
-// once, so a broken dependency costs one timeout, not one per item.
-__device__ __forceinline__ void wait_counter(const unsigned* ctr, unsigned target, int* err) {
-    if ((int)(ld_acquire(ctr) - target) >= 0) return;
-    const long long t0 = clock64();
-    while ((int)(ld_acquire(ctr) - target) < 0) {
-        if (*(volatile int*)err != 0) return;
-        __nanosleep(64);
-        if (clock64() - t0 > 2000000000LL) {
-            atomicExch(err, 1);
-            return;
-        }
-    }
-}
 
 struct Item {
     bool valid, isA;
@@ -215,7 +195,7 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
             float2* dst = S + b * P::SLOTP;
             if (it.isA) {
                 const int fb = it.plane / N, k = it.plane % N;
-                if (lane == 0 && use > 0) wait_counter(&doneB[r], use * P::NB, a.err);
+                if (lane == 0 && use > 0) wait_counter_bounded(&doneB[r], use * P::NB, a.err);
                 constexpr int NSL = FULL ? 2 : 1;                 // slabs per A item
                 constexpr int GN = FULL ? 2 * N : N;              // psi nodes of a grid row
                 if (a.grid_regular) {
@@ -241,7 +221,7 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
                 // B item: its W intermediate rows are contiguous in the ring (they stay in
                 // L2); one bulk copy brings them into the slot once the plane's A items
                 // are done, so the compute warps never wait on L2 latency themselves.
-                wait_counter(&doneA[r], (use + 1) * P::NA, a.err);
+                wait_counter_bounded(&doneA[r], (use + 1) * P::NA, a.err);
                 fence_proxy_async_global();          // the acquire above orders the copy's reads
                 mbar_arrive_expect_tx(&full[b], (uint32_t)(SLOT * 8));
                 bulk_g2s(dst, ring + ((size_t)(r * 2 + it.s) * N + it.pb * W) * N, (uint32_t)(SLOT * 8), &full[b]);

@@ -46,25 +46,8 @@ struct Cfg {
     static constexpr int BLOCKS_PER_SM = (N <= 256) ? 2 : 1;
 };
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
 __device__ __forceinline__ void discard_line(const void* p) {
     asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
-}
-__device__ __forceinline__ void wait_count(const unsigned* ctr, unsigned target, int* err) {
-    if ((int)(ld_acquire_u32(ctr) - target) >= 0) return;
-    const long long t0 = clock64();
-    while ((int)(ld_acquire_u32(ctr) - target) < 0) {
-        if (*(volatile int*)err != 0) return;
-        __nanosleep(64);
-        if (clock64() - t0 > 2000000000LL) {
-            atomicExch(err, 1);
-            return;
-        }
-    }
 }
 
 template <int N>
@@ -108,9 +91,9 @@ fft_inv_two_phase(BandArgs a, const float2* __restrict__ ws, float2* __restrict_
                 const int r = plane % RING;
                 const unsigned use = (unsigned)(plane / RING);
                 if (j < P::NA) {
-                    if (use > 0) wait_count(&doneB[r], use * P::NB, a.err);
+                    if (use > 0) wait_counter_bounded(&doneB[r], use * P::NB, a.err);
                 } else {
-                    wait_count(&doneA[r], (use + 1) * P::NA, a.err);
+                    wait_counter_bounded(&doneA[r], (use + 1) * P::NA, a.err);
                 }
             }
             *s_item = i;

@@ -29,6 +29,10 @@ bool fft_inverse_two_phase_supported(int N, bool fp64);
 cudaError_t launch_fft_inverse_two_phase(const BandArgs& a, const void* ws, void* grid, cudaStream_t st);
 cudaError_t launch_fft_inverse(const BandArgs& a, bool fp64, const void* ws, void* grid, cudaStream_t st);
 
+// One-block kernel whose bounded wait (kind 0: counter, 1: mbarrier) never
+// completes: it latches *err after about a second and returns.
+cudaError_t launch_bounded_wait_selftest(const unsigned* never, int* err, int kind, cudaStream_t st);
+
 // Stage 2: beta contraction with the recurrence fused in (forward), and the
 // transposed contraction (synthesis with weight 2l+1, or adjoint with weight
 // w_k/(2N^2)).
