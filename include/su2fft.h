@@ -225,7 +225,9 @@ su2_status su2_backward(su2_plan_t plan, const void* grad_coeffs, void* grad_gri
  * cannot allocate device memory at transform time need no workspace.
  *  - Plans whose su2_workspace_size exceeds SU2_NOALLOC_SCRATCH_BYTES are
  *    rejected with SU2_ERR_WORKSPACE (e.g. c64: one function up to N = 64).
- *  - No cudaMalloc / cudaFree or other allocation happens in this call.
+ *  - No cudaMalloc / cudaFree or other allocation happens in this call; a plan
+ *    created with SU2_FLAG_CUDA_GRAPH runs its kernels launch by launch here,
+ *    since recording and instantiating a graph would allocate.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) and caches it; make that first call before any
  *    stream capture.

@@ -531,6 +531,16 @@ su2_status check_exec(su2_plan_t plan, const void* in, const void* out, const vo
 }  // namespace
 
 namespace su2 {
+int forward_direct(su2_plan_s* plan, const void* grid, void* coeffs, void* ws, void* stream) {
+    su2_status s = check_exec(plan, grid, coeffs, ws);
+    if (s != SU2_OK) return s;
+    DeviceGuard g(plan->device);
+    if (!g.ok) return SU2_ERR_CUDA;
+    return from_cuda(enqueue_forward(plan, grid, coeffs, ws, (cudaStream_t)stream));
+}
+}  // namespace su2
+
+namespace su2 {
 int plan_device(const su2_plan_s* plan) { return plan ? plan->device : -1; }
 }  // namespace su2
 

@@ -52,5 +52,7 @@ extern "C" su2_status su2_forward_noalloc(su2_plan_t plan, const void* grid, voi
         g_scratch_ptr[plan_dev].store(p, std::memory_order_release);
         ptr = p;
     }
-    return su2_forward(plan, grid, coeffs, ptr, cuda_stream);
+    // launch by launch even for SU2_FLAG_CUDA_GRAPH plans: recording and
+    // instantiating a graph would allocate
+    return (su2_status)su2::forward_direct(plan, grid, coeffs, ptr, cuda_stream);
 }

@@ -56,5 +56,8 @@ bool encode_tensor_map_8b(CUtensorMap* map, int rank, const void* base, const cu
 
 // Device ordinal a plan's tables live on.
 int plan_device(const su2_plan_s* plan);
+// su2_forward's checks and launches, always enqueued launch by launch (never
+// recorded into a CUDA graph, whatever the plan's flags); returns an su2_status.
+int forward_direct(su2_plan_s* plan, const void* grid, void* coeffs, void* ws, void* stream);
 
 }  // namespace su2

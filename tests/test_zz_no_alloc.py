@@ -31,10 +31,13 @@ def _rel(a, b):
     return float((a - b).abs().max() / b.abs().max())
 
 
-@pytest.mark.parametrize("N,B,dtype,tol", [(32, 2, "c64", 1e-5), (64, 1, "c64", 1e-5), (16, 3, "c128", 1e-12)])
-def test_noalloc_matches_workspace_path(su2, N, B, dtype, tol):
+@pytest.mark.parametrize("N,B,dtype,tol,graph", [(32, 2, "c64", 1e-5, False), (64, 1, "c64", 1e-5, False),
+                                                 (16, 3, "c128", 1e-12, False), (32, 2, "c64", 1e-5, True)])
+def test_noalloc_matches_workspace_path(su2, N, B, dtype, tol, graph):
+    # graph=True: a plan that records su2_forward into a CUDA graph; the
+    # allocation-free call still launches its kernels one by one
     lib = su2.load()
-    plan = su2.Plan(N=N, batch=B, dtype=dtype)
+    plan = su2.Plan(N=N, batch=B, dtype=dtype, graph=graph)
     assert plan.workspace_bytes <= (4 << 20)
     td = torch.complex128 if dtype == "c128" else torch.complex64
     stream = torch.cuda.current_stream().cuda_stream
