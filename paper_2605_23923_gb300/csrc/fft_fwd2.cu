@@ -30,7 +30,12 @@
 // N points); weight w_k/(4N^2); origin phase (-1)^n and i (-1)^{n0}.
 //
 // CTA layout: warps 0 .. CT/32-1 compute, one producer warp issues the loads
-// (after the dependency waits) into a two-slot ring; mbarriers full/empty.
+// (after the dependency waits) into a two-slot ring (mbarriers full/empty), and
+// one signaller thread publishes the per-slot counters.  The compute warps hand
+// each finished phase to the signaller through a small record ring (mbarriers
+// sig_full/sig_empty); the signaller makes their global writes visible at GPU
+// scope (fence, cumulative over what it observed through the mbarrier) and
+// increments the counter, so no compute warp waits for its own stores to drain.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -48,20 +53,23 @@ namespace fwd2 {
 template <int N, bool FULL = false>
 struct Cfg {
     static constexpr int R1 = Radix<N>::R1, R2 = Radix<N>::R2;
+    static_assert(R1 >= R2, "pass a of both item kinds uses every compute thread");
     static constexpr int W = 16;                        // columns per A item, rows per B item
     static constexpr int NH = N / W;                    // A items per plane; B items per sector
     static constexpr int NA = NH, NB = 2 * NH, IB = NA + NB;
     static constexpr int CT = W * (R1 > R2 ? R1 : R2);  // compute threads
-    static constexpr int THREADS = CT + 32;
+    static constexpr int THREADS = CT + 64;             // + producer warp + signaller warp
     static constexpr int SLOT = W * N;                  // float2 of an A slab / B block
     static constexpr int PB = N + 1;                    // row pitch of a B block in the slot
     static constexpr int YP = SLOT + 16;                // B block with its pitch padding (128-B multiple)
     // full-group grid: an A slab holds both psi halves (columns j2 and j2 + N)
     static constexpr int SLOTP = (FULL ? 2 * SLOT : SLOT) + 16;   // slot stride
     static constexpr int NS = 2;                        // ring slots
+    static constexpr int NR = 4;                        // signal records
     static constexpr int BOXR = N < 256 ? N : 256;      // rows per TMA box (at most 256)
     static constexpr size_t smem_bytes() {
-        return (size_t)NS * SLOTP * 8 + (size_t)YP * 8 + (size_t)N * 8 * 3 + (size_t)N * 4 + 2 * NS * 8 + NS * 4;
+        return (size_t)NS * SLOTP * 8 + (size_t)YP * 8 + (size_t)N * 8 * 3 + (size_t)N * 4 + 2 * NS * 8 + 2 * NR * 8 +
+               NS * 4 + NR * 4;
     }
     static constexpr int BLOCKS_PER_SM =
         FULL ? (N <= 128 ? 2 : 1) : ((N <= 64) ? 4 : (N <= 128) ? 3 : (N <= 256 ? 2 : 1));
@@ -136,7 +144,10 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
     float* wk = reinterpret_cast<float*>(omq + N);
     uint64_t* full = reinterpret_cast<uint64_t*>(wk + N);      // [NS]
     uint64_t* empty = full + NS;                               // [NS]
-    int* slot_item = reinterpret_cast<int*>(empty + NS);       // [NS] item held by a slot (-1: end)
+    uint64_t* sig_full = empty + NS;                           // [NR]
+    uint64_t* sig_empty = sig_full + P::NR;                    // [NR]
+    int* slot_item = reinterpret_cast<int*>(sig_empty + P::NR);   // [NS] item held by a slot (-1: end)
+    int* sig_rec = slot_item + NS;                             // [NR] counter to increment (-1: end)
 
     const int tid = threadIdx.x;
     const int nplanes = a.nfunc * N;
@@ -157,9 +168,30 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
             mbar_init(&full[b], 1);
             mbar_init(&empty[b], CT / 32);
         }
+        for (int j = 0; j < P::NR; ++j) {
+            mbar_init(&sig_full[j], 1);
+            mbar_init(&sig_empty[j], 1);
+        }
         mbar_fence_init();
     }
     __syncthreads();
+
+    if (tid >= CT + 32) {
+        // ------------------------------------------------------------ signaller
+        // Record c: counter index (doneA: r, doneB: RING + r) of a phase whose
+        // global effects every compute thread has issued before thread 0's arrive.
+        if (tid != CT + 32) return;
+        for (int c = 0;; ++c) {
+            const int j = c % P::NR;
+            if (!mbar_wait_bounded(&sig_full[j], (unsigned)(c / P::NR) & 1, a.err)) break;
+            const int rec = sig_rec[j];
+            mbar_arrive_cta(&sig_empty[j]);
+            if (rec < 0) break;
+            __threadfence();
+            atomicAdd(&doneA[rec], 1u);            // doneB follows doneA in memory
+        }
+        return;
+    }
 
     if (tid >= CT) {
         // ------------------------------------------------------------- producer
@@ -232,7 +264,16 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
     }
 
     // ----------------------------------------------------------------- compute
-    const int warp = tid >> 5, lane = tid & 31;
+    const int lane = tid & 31;
+    int nrec = 0;                                  // records pushed (thread 0)
+    auto push = [&](int rec) {                     // thread 0, after a barrier of all compute threads
+        const int j = nrec % P::NR;
+        const unsigned v = (unsigned)(nrec / P::NR);
+        ++nrec;
+        if (v > 0) mbar_wait_bounded(&sig_empty[j], (v - 1) & 1, a.err);
+        sig_rec[j] = rec;
+        mbar_arrive_cta(&sig_full[j]);
+    };
     int n = 0;
     for (;;) {
         const int b = n % NS;
@@ -267,12 +308,10 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
 #pragma unroll
                 for (int q = 0; q < R2; ++q) Y[(ia + R1 * q) * W + jc] = (q == 0) ? w[0] : cmul(w[q], om[ia * q]);
                 dft_reg<R2, 1, float>(v);
-                named_sync(1, CT);
+                // written back to the positions this thread read: no barrier needed before
 #pragma unroll
                 for (int q = 0; q < R2; ++q) X[(ia + R1 * q) * W + jc] = (q == 0) ? v[0] : cmul(v[q], om[ia * q]);
                 fence_proxy_async_smem();   // before the slot is refilled by TMA
-            } else {
-                named_sync(1, CT);
             }
             named_sync(1, CT);
             // Pass b: R1-point DFTs over ia; bin p = qb + R2*qa -> intermediate row p.
@@ -294,14 +333,12 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
             }
             named_sync(1, CT);                   // slot and Y read; intermediate written
             if (lane == 0) mbar_arrive_cta(&empty[b]);
-            if (tid == 0) {
-                __threadfence();
-                atomicAdd(&doneA[r], 1u);
-            }
+            if (tid == 0) push(r);               // doneA[r]
         } else {
             // Pass a: R2-point DFTs over j2 = ia + R1*q of row pl, from the rows the
-            // producer copied into the slot (pitch N); written back with the odd row
-            // pitch N + 1.
+            // producer copied into the slot (pitch N), into Y with the odd row pitch
+            // N + 1 (Y is free during B items), so the slot is released after one
+            // barrier.
             const float2* rows = ring + ((size_t)(r * 2 + it.s) * N + it.pb * W) * N;
             {
                 const int ia = tid % R1, pl = tid / R1;            // W * R1 == CT
@@ -315,29 +352,24 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
                 dft_reg<R2, 1, float>(v);
 #pragma unroll
                 for (int q = 1; q < R2; ++q) v[q] = cmul(v[q], omq[q * R1 + ia]);
-                named_sync(1, CT);        // every load of the item has been consumed
 #pragma unroll
-                for (int q = 0; q < R2; ++q) X[pl * P::PB + ia + R1 * q] = v[q];   // odd pitch: no conflicts
-                fence_proxy_async_smem();   // before the slot is refilled by TMA
+                for (int q = 0; q < R2; ++q) Y[pl * P::PB + ia + R1 * q] = v[q];   // odd pitch: no conflicts
             }
-            // The rows are in registers / shared memory: drop them from L2, release them.
+            // The rows are in shared memory: drop them from L2, release them.
             if (discard_ok) {             // ring rows on 128-byte lines: no line is shared
                 const char* src = reinterpret_cast<const char*>(rows);
                 for (int l = tid; l < SLOT * 8 / 128; l += CT) discard_l2_line(src + (size_t)l * 128);
             }
-            named_sync(1, CT);
-            if (tid == 0) {
-                __threadfence();
-                atomicAdd(&doneB[r], 1u);
-            }
+            named_sync(1, CT);            // slot read, Y written, discards issued
+            if (lane == 0) mbar_arrive_cta(&empty[b]);
+            if (tid == 0) push(RING + r);        // doneB[r]
             // Pass b: R1-point DFTs; output bin q = qb + R2*qa; 16 consecutive ni per row.
             if (tid < W * R2) {
                 const int pl = tid % W, qb = tid / W;
                 float2 v[R1];
 #pragma unroll
-                for (int ia = 0; ia < R1; ++ia) v[ia] = X[pl * P::PB + ia + R1 * qb];
-                named_sync(2, W * R2);
-                if (lane == 0) mbar_arrive_cta(&empty[b]);
+                for (int ia = 0; ia < R1; ++ia) v[ia] = Y[pl * P::PB + ia + R1 * qb];
+                named_sync(2, CT);        // Y read before the next item rewrites it
                 dft_reg<R1, 1, float>(v);
                 const float scale = wk[k] / ((FULL ? 4.f : 2.f) * (float)N * (float)N);
                 const size_t plane_off = a.grid_regular ? a.ws_group_off + (size_t)fb * 2 * N * N * N
@@ -381,11 +413,12 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
                 else
                     store_all(ws + plane_off + ((size_t)k * 2 + it.s) * N * N + ni,
                               std::integral_constant<size_t, (size_t)N>());
-                        } else if (lane == 0 && (warp * 32) >= W * R2) {
-                mbar_arrive_cta(&empty[b]);
+            } else {
+                named_sync(2, CT);
             }
         }
     }
+    if (tid == 0) push(-1);                       // end of the signaller's records
 }
 
 // Work-distribution parameters shared by the plan (workspace size) and the launch.
