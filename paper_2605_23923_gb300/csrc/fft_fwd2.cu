@@ -83,6 +83,20 @@ __device__ __forceinline__ void tma_load_3d_hint(void* dst, const CUtensorMap* m
         ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar)), "l"(policy)
         : "memory");
 }
+// Tensor store of a box from this CTA's shared memory (bulk async-group) with an
+// L2 eviction policy.  The planes take evict-first: with the default policy a
+// line of the tile-major planes (four beta nodes, written by four B items) was
+// often written back before it was complete, 18% more DRAM traffic.
+__device__ __forceinline__ void tma_store_5d(const CUtensorMap* map, const void* src, int c0, int c1, int c2, int c3,
+                                             int c4, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.global.shared::cta.bulk_group.L2::cache_hint [%0, {%1, %2, %3, %4, %5}], [%6], %7;"
+        ::"l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(src)), "l"(policy)
+        : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ uint64_t policy_evict_first() {
     uint64_t p;
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
@@ -131,8 +145,8 @@ __device__ __forceinline__ Item decode(int i, int nplanes, int D) {
 
 template <int N, bool FULL>
 __global__ void __launch_bounds__(Cfg<N, FULL>::THREADS, Cfg<N, FULL>::BLOCKS_PER_SM)
-fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const float2* __restrict__ grid,
-                  float2* __restrict__ ws, int D, int RING, int discard_ok) {
+fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const __grid_constant__ CUtensorMap omap,
+                  const float2* __restrict__ grid, float2* __restrict__ ws, int D, int RING, int discard_ok, int ostore) {
     using P = Cfg<N, FULL>;
     constexpr int R1 = P::R1, R2 = P::R2, W = P::W, CT = P::CT, SLOT = P::SLOT, NS = P::NS;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -197,6 +211,26 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
         // ------------------------------------------------------------- producer
         const int lane = tid - CT;
         const uint64_t pol = policy_evict_first();
+        // ostore: a B item leaves its output block (N rows mi x W columns ni, one
+        // plane k, one sector) in its slot, and this warp writes it to the planes
+        // with tensor stores before the slot is refilled.  pend(b): that B item.
+        static_assert(NS == 2, "one pending block per slot, held in two registers");
+        int pend0 = -1, pend1 = -1;
+        auto pend = [&](int j) -> int& { return j ? pend1 : pend0; };
+        auto store_block = [&](int item, const float2* src) {      // lane 0
+            const Item ob = decode<N>(item, nplanes, D);
+            const int fb = ob.plane / N, k = ob.plane % N;
+            const int ni0 = (ob.pb * W + N / 2) & (N - 1);
+#pragma unroll
+            for (int h = 0; h < N / P::BOXR; ++h) {
+                if (a.ws_tile_major)       // [fb*2 + s][mi][ni/4][k][ni%4]
+                    tma_store_5d(&omap, src + h * P::BOXR * W, 0, k, ni0 / 4, h * P::BOXR, fb * 2 + ob.s, pol);
+                else                       // [fb][k][s][mi][ni]
+                    tma_store_5d(&omap, src + h * P::BOXR * W, ni0, h * P::BOXR, ob.s, k, fb, pol);
+            }
+            bulk_commit();
+            bulk_wait_read_all();          // the slot may be refilled once the box is read
+        };
         int n = 0;
         for (;;) {
             // Items are handed out in number order, so every item this CTA waits
@@ -212,15 +246,27 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
             const unsigned u = (unsigned)(n / NS);
             ++n;
             if (u > 0 && !mbar_wait_bounded(&empty[b], (u - 1) & 1, a.err)) i = nitems;
+            if (lane == 0 && pend(b) >= 0) {
+                store_block(pend(b), S + b * P::SLOTP);
+                pend(b) = -1;
+            }
             if (i >= nitems) {
                 if (lane == 0) {
                     slot_item[b] = -1;
                     mbar_arrive_cta(&full[b]);
+                    // the other slot's last item, once its block is staged
+                    const int b2 = n % NS;
+                    if (pend(b2) >= 0 && mbar_wait_bounded(&empty[b2], (unsigned)((n - 2) / NS) & 1, a.err))
+                        store_block(pend(b2), S + b2 * P::SLOTP);
+                    bulk_wait_all();
                 }
                 break;
             }
             const Item it = decode<N>(i, nplanes, D);
-            if (lane == 0) slot_item[b] = i;          // published by the arrive on full[b]
+            if (lane == 0) {
+                slot_item[b] = i;                     // published by the arrive on full[b]
+                if (ostore && !it.isA) pend(b) = i;
+            }
             __syncwarp();
             const int r = it.plane % RING;
             const unsigned use = (unsigned)(it.plane / RING);
@@ -361,7 +407,7 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
                 for (int l = tid; l < SLOT * 8 / 128; l += CT) discard_l2_line(src + (size_t)l * 128);
             }
             named_sync(1, CT);            // slot read, Y written, discards issued
-            if (lane == 0) mbar_arrive_cta(&empty[b]);
+            if (!ostore && lane == 0) mbar_arrive_cta(&empty[b]);
             if (tid == 0) push(RING + r);        // doneB[r]
             // Pass b: R1-point DFTs; output bin q = qb + R2*qa; 16 consecutive ni per row.
             if (tid < W * R2) {
@@ -406,15 +452,32 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const fl
                         __stcs(dst, val);
                     }
                 };
-                if (a.ws_tile_major)
+                if (ostore) {
+                    // block [mi][pl] in the slot (rows of W consecutive ni); the producer
+                    // writes it out with tensor stores
+#pragma unroll
+                    for (int qa = 0; qa < R1; ++qa) {
+                        float2 val = rot ? make_float2(-v[qa].y * sc, v[qa].x * sc)
+                                         : make_float2(v[qa].x * sc, v[qa].y * sc);
+                        if (zero_col || (zero_nyq && qa == R1 / 2)) val = make_float2(0.f, 0.f);
+                        const int mi = qb + R2 * qa + ((qa < R1 / 2) ? N / 2 : -N / 2);
+                        X[mi * W + pl] = val;
+                    }
+                    fence_proxy_async_smem();
+                } else if (a.ws_tile_major) {
                     store_all(ws + plane_off + (size_t)it.s * N * N * N + (size_t)(ni >> 2) * N * 4 + (size_t)k * 4 +
                                   (ni & 3),
                               std::integral_constant<size_t, (size_t)N * N>());
-                else
+                } else {
                     store_all(ws + plane_off + ((size_t)k * 2 + it.s) * N * N + ni,
                               std::integral_constant<size_t, (size_t)N>());
+                }
             } else {
                 named_sync(2, CT);
+            }
+            if (ostore) {                 // block staged: hand the slot to the producer
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cta(&empty[b]);
             }
         }
     }
@@ -472,8 +535,28 @@ static cudaError_t launch_n(const BandArgs& a, const void* in, void* out, cudaSt
         if (c >= 1 && c < grid) grid = c;
     }
     const int discard_ok = ((uintptr_t)ring % 128) == 0;
-    fft_fwd_two_phase<N, FULL><<<grid, P::THREADS, P::smem_bytes(), st>>>(b, gmap, (const float2*)in, (float2*)out,
-                                                                         D, RING, discard_ok);
+    // Output planes of the group (function i at ws_group_off + 2 N^3 i) as a 5-D
+    // tensor for the B items' tensor stores; boxes of BOXR rows mi x W columns ni.
+    CUtensorMap omap;
+    memset(&omap, 0, sizeof(omap));
+    int ostore = 0;
+    if (b.grid_regular) {
+        const cuuint64_t n = (cuuint64_t)N, e = 8;
+        const void* base = (const float2*)out + a.ws_group_off;
+        if (a.ws_tile_major) {         // [fb*2 + s][mi][ni/4][k][ni%4]
+            const cuuint64_t dims[5] = {4, n, n / 4, n, 2 * (cuuint64_t)a.nfunc};
+            const cuuint64_t strides[4] = {4 * e, 4 * n * e, n * n * e, n * n * n * e};
+            const cuuint32_t box[5] = {4, 1, (cuuint32_t)P::W / 4, (cuuint32_t)P::BOXR, 1};
+            ostore = encode_tensor_map_8b(&omap, 5, base, dims, strides, box) ? 1 : 0;
+        } else {                       // [fb][k][s][mi][ni]
+            const cuuint64_t dims[5] = {n, n, 2, n, (cuuint64_t)a.nfunc};
+            const cuuint64_t strides[4] = {n * e, n * n * e, 2 * n * n * e, 2 * n * n * n * e};
+            const cuuint32_t box[5] = {(cuuint32_t)P::W, (cuuint32_t)P::BOXR, 1, 1, 1};
+            ostore = encode_tensor_map_8b(&omap, 5, base, dims, strides, box) ? 1 : 0;
+        }
+    }
+    fft_fwd_two_phase<N, FULL><<<grid, P::THREADS, P::smem_bytes(), st>>>(b, gmap, omap, (const float2*)in,
+                                                                         (float2*)out, D, RING, discard_ok, ostore);
     return cudaGetLastError();
 }
 
