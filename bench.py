@@ -41,10 +41,10 @@ FP32_LANES = 128
 # dram__bytes_write.sum of one launch / 8), valid only while the kernel's
 # sources are unchanged (hash of the listed files at capture time).
 PROFILED_TRAFFIC = {
-    "fft_fwd_two_phase": {"N": 256, "bytes_per_function": (1.074982e9 + 2.183300e9) / 8,
-                          "sources": ("fft_fwd2.cu", "common.cuh"), "sha": "f1453db5389e8526"},
-    "contract_tc_kernel": {"N": 256, "bytes_per_function": (2.146820e9 + 0.356383e9) / 8,
-                           "sources": ("contract_tc.cu", "recurrence.cuh", "common.cuh"), "sha": "7cbcf9163fe88173"},
+    "fft_fwd_two_phase": {"N": 256, "bytes_per_function": (1.074314e9 + 2.182385e9) / 8,
+                          "sources": ("fft_fwd2.cu", "common.cuh"), "sha": "e4edfdb431ea03a9"},
+    "contract_tc_kernel": {"N": 256, "bytes_per_function": (2.145987e9 + 0.356537e9) / 8,
+                           "sources": ("contract_tc.cu", "recurrence.cuh", "common.cuh"), "sha": "17ab2f11fe450921"},
 }
 
 
@@ -504,9 +504,22 @@ def main():
         b_.record(stream)
         torch.cuda.synchronize()
         ems = max_over_ranks(a.elapsed_time(b_), world, dev)
+        # the copies alone, for context (outside the timed region): one upload of the
+        # batch's grids and one download of its coefficients, back to back on the stream
+        c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        c0.record(stream)
+        dgrid.copy_(host_grid, non_blocking=True)
+        c1.record(stream)
+        host_out.copy_(out, non_blocking=True)
+        c2.record(stream)
+        torch.cuda.synchronize()
+        up_ms, down_ms = c0.elapsed_time(c1), c1.elapsed_time(c2)
         e2e = {"value": whole_job_value(world, B, args.e2e_steps, ems), "unit": UNIT,
                "h2d_bytes_per_step": host_grid.numel() * 8, "d2h_bytes_per_step": host_out.numel() * 8,
-               "steps": args.e2e_steps}
+               "steps": args.e2e_steps,
+               "copies_alone": {"h2d_GB/s": host_grid.numel() * 8 / up_ms / 1e6,
+                                "d2h_GB/s": host_out.numel() * 8 / down_ms / 1e6,
+                                "ms_upload_then_download": up_ms + down_ms}}
         del host_grid, host_out, dgrid
 
     if rank != 0:

@@ -112,6 +112,29 @@ template <typename T> __device__ __forceinline__ T tw32_sin(int t) {
     return T(0);
 }
 
+// Ratio used by the tangent-form butterfly for t = 1..15, t != 8 (omega_32^t =
+// cos + i sin): tan(2 pi t/32) where |cos| >= |sin| (t <= 4 or t >= 12), else
+// cot(2 pi t/32); both in [-1, 1].
+template <typename T> __device__ __forceinline__ T tw32_ratio(int t) {
+    switch (t & 31) {
+    case 1: return T(0.19891236737965800691);
+    case 2: return T(0.41421356237309504880);
+    case 3: return T(0.66817863791929892000);
+    case 4: return T(1.0000000000000000000);
+    case 5: return T(0.66817863791929892000);
+    case 6: return T(0.41421356237309504880);
+    case 7: return T(0.19891236737965800691);
+    case 9: return T(-0.19891236737965800691);
+    case 10: return T(-0.41421356237309504880);
+    case 11: return T(-0.66817863791929892000);
+    case 12: return T(-1.0000000000000000000);
+    case 13: return T(-0.66817863791929892000);
+    case 14: return T(-0.41421356237309504880);
+    case 15: return T(-0.19891236737965800691);
+    }
+    return T(0);
+}
+
 __host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n >> 1); }
 __host__ __device__ __forceinline__ constexpr int bitrev(int i, int bits) {
     int r = 0;
@@ -135,19 +158,25 @@ __device__ __forceinline__ void dft_stage(cplx<T> (&y)[R]) {
             for (int k = 0; k < half; ++k) {
                 const int t = k * step;
                 const cplx<T> b = y[i + k + half];
-                cplx<T> tb;
-                if (t == 0) {
-                    tb = b;
-                } else if (t == 8) {            // omega = SIGN * i
-                    tb = (SIGN > 0) ? mk<T>(-b.y, b.x) : mk<T>(b.y, -b.x);
+                const cplx<T> a = y[i + k];
+                if (t == 0 || t == 8) {
+                    // omega = 1 or SIGN * i: additions only
+                    const cplx<T> tb = (t == 0) ? b : ((SIGN > 0) ? mk<T>(-b.y, b.x) : mk<T>(b.y, -b.x));
+                    y[i + k] = cadd(a, tb);
+                    y[i + k + half] = csub(a, tb);
                 } else {
+                    // a +- omega b with omega = c + i sn in the tangent form: omega b = g u with
+                    // u = b + i (sn/c) b, g = c when |c| >= |sn|, else u = i b + (c/sn) b,
+                    // g = sn (ratio in [-1, 1]); then 2 + 4 fused multiply-adds instead of 8
                     const T c = tw32_cos<T>(t);
                     const T sn = (SIGN > 0) ? tw32_sin<T>(t) : -tw32_sin<T>(t);
-                    tb = mk<T>(b.x * c - b.y * sn, b.x * sn + b.y * c);
+                    const bool cdom = (t <= 4 || t >= 12);      // |cos| >= |sin| (t < 16)
+                    const T r = (SIGN > 0) ? tw32_ratio<T>(t) : -tw32_ratio<T>(t);
+                    const T g = cdom ? c : sn;
+                    const cplx<T> u = cdom ? mk<T>(b.x - r * b.y, b.y + r * b.x) : mk<T>(r * b.x - b.y, b.x + r * b.y);
+                    y[i + k] = mk<T>(a.x + g * u.x, a.y + g * u.y);
+                    y[i + k + half] = mk<T>(a.x - g * u.x, a.y - g * u.y);
                 }
-                const cplx<T> a = y[i + k];
-                y[i + k] = cadd(a, tb);
-                y[i + k + half] = csub(a, tb);
             }
         }
         dft_stage<R, SIGN, T, LEN * 2>(y);
