@@ -114,12 +114,14 @@ __device__ __forceinline__ void named_sync(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+// 5-D tensor load with an L2 policy (the planes are read once: evict-first).
 __device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4,
-                                            uint64_t* bar) {
+                                            uint64_t* bar, uint64_t policy) {
     asm volatile(
-        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-        "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
-        ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint "
+        "[%0], [%1, {%2, %3, %4, %5, %6}], [%7], %8;"
+        ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar)),
+          "l"(policy)
         : "memory");
 }
 
@@ -203,6 +205,8 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
     if (warp == W_TMA) {
         // ------------------------------------------------------------------ TMA
         if (lane == 0) {
+            uint64_t pol;
+            asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
             uint32_t g = 0;
             for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
                 Tile<NP> tl;
@@ -215,7 +219,7 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
                     if (u > 0) mbar_wait_bounded(&bar_sfree[st], (u - 1) & 1, a.err);
                     mbar_arrive_expect_tx(&bar_full[st], (uint32_t)STAGE_BYTES);
                     tma_load_5d(smem + OFF_STG + st * STAGE_BYTES, &tmap, c * KC * NP, tl.nb, tl.mi, tl.s, bb * BM,
-                                &bar_full[st]);
+                                &bar_full[st], pol);
                 }
             }
         }
@@ -470,7 +474,7 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
                             if (pp == pt) { re = vr; im = vi; }
                         }
                         if (r < Lt && okh[h] && vt && J >= mu2t)
-                            cfh[h][rowbase + (n2t + J) / 2] = cmul_ipow(make_float2(re, im), ipw);
+                            __stcs(&cfh[h][rowbase + (n2t + J) / 2], cmul_ipow(make_float2(re, im), ipw));   // written once
                     }
                 }
             }
