@@ -68,11 +68,13 @@ static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 constexpr uint32_t TMEM_COLS = 512;         // 4 pairs x 128 columns, or two halves of 4 x 64
 // Accumulator placement: a tile with at most 64 rows of l ("small") takes one
 // half of tensor memory (pairs 64 columns apart), alternating halves, so its
-// MMAs overlap the epilogue of the previous tile; a larger tile takes both.
+// MMAs overlap the epilogue of the previous tile; a larger tile takes both
+// (pair p at column 128 p) and its epilogue drains pairs 0, 1 first and frees
+// half 0 before it reads pairs 2, 3, so the next tile starts in half 0.
 __device__ __forceinline__ void acc_place(int nmma, int& nexth, int& h0, bool& big) {
     big = nmma > 64;
     h0 = big ? 0 : nexth;
-    if (!big) nexth ^= 1;
+    nexth = big ? 0 : (nexth ^ 1);     // after a big tile, half 0 (drained first) comes next
 }
 
 __device__ __forceinline__ int a_off(int row, int kk) {
@@ -440,6 +442,47 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
             // After the TMEM load lane l holds row 32q + l (function 16q + l/2, re or im)
             // for the 4 pairs.  For the stores, lane t takes function 16q + 8h + t/4 and
             // pair t%4 (h = 0, 1), so 4 adjacent lanes write 4 consecutive n.
+            if (big) {
+                // two halves: pairs 0, 1 (columns 0..255) then pairs 2, 3; half 0 is
+                // released as soon as it is drained.  Lane t: function 16q + t/2, pair
+                // 2g + t%2, so 2 adjacent lanes write 2 consecutive n.
+                const int fb2 = bb * BM + 16 * q + (lane >> 1);
+                const bool ok2 = fb2 < a.nfunc;
+                float2* cf2 = coeffs + (ok2 ? a.coeff_off[a.fidx[fb2]] : 0);
+                const int src2 = 2 * (lane >> 1);
+#pragma unroll 1
+                for (int g = 0; g < 2; ++g) {
+                    const int p2 = 2 * g + (lane & 1);
+                    const int n2t = tl.n2[p2], mu2t = tl.mu2[p2];
+                    const bool vt = tl.valid[p2] && ok2;
+                    const int ipw = (n2t - tl.m2) / 2;
+                    for (int cc = 0; cc < nmma; cc += 16) {
+                        uint32_t rv[2][16];
+#pragma unroll
+                        for (int pp = 0; pp < 2; ++pp)
+                            tmem_ld16(base + (uint32_t)(2 * g + pp) * 128u + (uint32_t)cc, rv[pp]);
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const int r = cc + j;
+                            const int J = tl.j0 + 2 * r;
+                            const size_t rowbase =
+                                (size_t)t_rowoff[J < N ? J : N - 1] + (size_t)((tl.m2 + J) / 2) * (J + 1);
+                            const float r0 = __shfl_sync(0xffffffffu, __uint_as_float(rv[0][j]), src2);
+                            const float i0 = __shfl_sync(0xffffffffu, __uint_as_float(rv[0][j]), src2 + 1);
+                            const float r1 = __shfl_sync(0xffffffffu, __uint_as_float(rv[1][j]), src2);
+                            const float i1 = __shfl_sync(0xffffffffu, __uint_as_float(rv[1][j]), src2 + 1);
+                            const float re = (lane & 1) ? r1 : r0, im = (lane & 1) ? i1 : i0;
+                            if (r < Lt && vt && J >= mu2t)
+                                __stcs(&cf2[rowbase + (n2t + J) / 2], cmul_ipow(make_float2(re, im), ipw));
+                        }
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&bar_hfree[g]);
+                }
+                continue;
+            }
             const int pt = lane & 3;
             float2* cfh[2];
             bool okh[2];
