@@ -50,7 +50,36 @@ struct Band {
     float2* d_lit_twist = nullptr;
     int s1_two_phase = 0;         // kernel choices (defaults, or the autotuner's)
     int s2_bt = 0;
+    int* d_s2_tiles = nullptr;    // FP32 contraction tiles grouped by rows of l (see BandArgs)
+    int s2_ntiles[3] = {0, 0, 0};
 };
+
+// Tiles of 4 consecutive n at fixed (sector, m) for the FP32 contraction, grouped
+// by their number of rows of l (L <= 32, 32 < L <= 64, L > 64), so that each
+// group runs with a row window that fits it; tiles without a coefficient are left
+// out.  The numbering and L follow the device-side tile decode.
+void fp32_tile_classes(int N, std::vector<int>& tiles, int counts[3]) {
+    std::vector<int> cls[3];
+    const int nbk = N / 4;
+    for (int t = 0; t < 2 * N * nbk; ++t) {
+        const int nb = t % nbk, mi = (t / nbk) % N, s = t / (nbk * N);
+        const int m2 = 2 * (mi - N / 2) + s, jtop = N - 2 + s;
+        int j0 = 1 << 30;
+        for (int p = 0; p < 4; ++p) {
+            const int ni = nb * 4 + p, n2 = 2 * (ni - N / 2) + s;
+            const bool valid = !(s == 0 && mi == 0) && !(s == 0 && ni == 0);
+            if (valid) j0 = std::min(j0, std::max(std::abs(n2), std::abs(m2)));
+        }
+        if (j0 == (1 << 30)) continue;
+        const int L = (jtop - j0) / 2 + 1;
+        cls[L <= 32 ? 0 : (L <= 64 ? 1 : 2)].push_back(t);
+    }
+    tiles.clear();
+    for (int c = 0; c < 3; ++c) {
+        counts[c] = (int)cls[c].size();
+        tiles.insert(tiles.end(), cls[c].begin(), cls[c].end());
+    }
+}
 
 struct DeviceGuard {
     int prev = -1;
@@ -190,6 +219,11 @@ cudaError_t build_band(su2_plan_s* P, Band& b) {
     }
     cudaError_t e;
     if ((e = P->upload(&b.d_fidx, b.fids.data(), b.fids.size())) != cudaSuccess) return e;
+    if (P->dtype == SU2_C64 && !b.tc && !b.literal) {
+        std::vector<int> tiles;
+        fp32_tile_classes(N, tiles, b.s2_ntiles);
+        if ((e = P->upload(&b.d_s2_tiles, tiles.data(), tiles.size())) != cudaSuccess) return e;
+    }
     if ((e = P->upload(&b.d_cosb, cosb.data(), N)) != cudaSuccess) return e;
     if ((e = P->upload(&b.d_log2c, l2c.data(), N)) != cudaSuccess) return e;
     if ((e = P->upload(&b.d_log2s, l2s.data(), N)) != cudaSuccess) return e;
@@ -270,6 +304,8 @@ su2::BandArgs band_args(const su2_plan_s* P, const Band& b) {
     a.literal = b.literal ? 1 : 0;
     a.lit_w = b.d_lit_w;
     a.lit_twist = b.d_lit_twist;
+    a.s2_tiles = b.d_s2_tiles;
+    for (int c = 0; c < 3; ++c) a.s2_ntiles[c] = b.s2_ntiles[c];
     const size_t n3 = (b.full_group ? 2 : 1) * (size_t)b.N * b.N * b.N;   // elements of one grid
     for (size_t i = 0; i < b.fids.size(); ++i)
         if (P->grid_off[b.fids[i]] != a.grid_group_off + i * n3) a.grid_regular = 0;

@@ -371,6 +371,9 @@ struct BandArgs {
                                   // aux_ring then counts the literal kernel's CTAs (one N^2 slab each)
     const float2* lit_w;          // [N][N] e^{2 pi i (r - N/2) t/(N-1)}, column N-1 zero (literal grid)
     const float2* lit_twist;      // [2N] e^{i pi u/(N-1)} (literal grid)
+    const int* s2_tiles;          // FP32 contraction tiles by rows of l: L <= 32, then 32 < L <= 64,
+                                  // then L > 64, concatenated (tile numbers as Tile<4>::decode takes)
+    int s2_ntiles[3];             // tiles in each of those classes
 };
 
 }  // namespace su2

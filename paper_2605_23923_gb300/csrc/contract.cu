@@ -58,14 +58,15 @@ struct FwdCfg {
 
 template <typename T, int NB, int BT, int KC, int LW, int ML, int MB>
 __global__ void __launch_bounds__(FwdCfg<T, NB, BT, KC, LW, ML, MB>::THREADS)
-contract_fwd(BandArgs a, const cplx<T>* __restrict__ F2, cplx<T>* __restrict__ coeffs) {
+contract_fwd(BandArgs a, const cplx<T>* __restrict__ F2, cplx<T>* __restrict__ coeffs,
+             const int* __restrict__ tiles) {
     using Cx = cplx<T>;
     using Cfg = FwdCfg<T, NB, BT, KC, LW, ML, MB>;
     constexpr int THREADS = Cfg::THREADS, LDD = Cfg::LDD;
     static_assert(NB * KC <= THREADS, "one generator thread per (pair, node)");
     const int N = a.N;
     Tile<NB> tl;
-    tl.decode(N, blockIdx.x);
+    tl.decode(N, tiles ? tiles[blockIdx.x] : (int)blockIdx.x);   // tiles: one row class of them
     if (!tl.any) return;
     const int bb = blockIdx.y;
     const int r0 = blockIdx.z * LW;
@@ -498,23 +499,39 @@ contract_tr32(BandArgs a, int mode, const float2* __restrict__ coeffs, float2* _
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
+// tile_list / ntiles: launch over the listed tiles only (one row class), else over all
 template <typename T, int NB, int BT, int KC, int LW, int ML, int MB>
-static cudaError_t launch_fwd_t(const BandArgs& a, const void* ws, void* coeffs, cudaStream_t st) {
+static cudaError_t launch_fwd_t(const BandArgs& a, const void* ws, void* coeffs, cudaStream_t st,
+                                const int* tile_list = nullptr, int ntiles = 0) {
     using Cfg = FwdCfg<T, NB, BT, KC, LW, ML, MB>;
     auto kern = contract_fwd<T, NB, BT, KC, LW, ML, MB>;
     const size_t smem = Cfg::smem_bytes(a.N);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int tiles = 2 * a.N * (a.N / NB);
+    const int tiles = tile_list ? ntiles : 2 * a.N * (a.N / NB);
+    if (tiles <= 0) return cudaSuccess;
     const int windows = (a.N / 2 + LW - 1) / LW;
     dim3 g(tiles, (a.nfunc + BT - 1) / BT, windows);
-    kern<<<g, Cfg::THREADS, smem, st>>>(a, (const cplx<T>*)ws, (cplx<T>*)coeffs);
+    kern<<<g, Cfg::THREADS, smem, st>>>(a, (const cplx<T>*)ws, (cplx<T>*)coeffs, tile_list);
     return cudaGetLastError();
 }
 
 cudaError_t launch_contract_forward(const BandArgs& a, bool fp64, const void* ws, void* coeffs, cudaStream_t st) {
     if (a.nfunc <= 0) return cudaSuccess;
     if (fp64) return launch_fwd_t<double, 4, 8, 32, 64, 4, 2>(a, ws, coeffs, st);
+    if (a.s2_tiles && a.nfunc >= 48) {
+        // Large batches: one launch per row class, each with a row window that fits
+        // its tiles (32, 64, 128 rows of l) and the threads that a window of all 128
+        // rows would leave idle on short tiles spent on more functions (64, 32, 16
+        // per block; 256 threads each).
+        const int* t0 = a.s2_tiles;
+        const int* t1 = t0 + a.s2_ntiles[0];
+        const int* t2 = t1 + a.s2_ntiles[1];
+        cudaError_t e = launch_fwd_t<float, 4, 64, 32, 32, 8, 4>(a, ws, coeffs, st, t0, a.s2_ntiles[0]);
+        if (e == cudaSuccess) e = launch_fwd_t<float, 4, 32, 32, 64, 8, 4>(a, ws, coeffs, st, t1, a.s2_ntiles[1]);
+        if (e == cudaSuccess) e = launch_fwd_t<float, 4, 16, 32, 128, 8, 4>(a, ws, coeffs, st, t2, a.s2_ntiles[2]);
+        return e;
+    }
     // 8 or 16 functions per block (chosen by the plan's autotuner, else by batch
     // size: small batches take 8 so that no FMA lane works on padding)
     const int bt = a.s2_bt ? a.s2_bt : (a.nfunc <= 8 ? 8 : 16);
