@@ -52,9 +52,20 @@ struct FwdCfg {
     static constexpr int LDD = LW + 4;
     static size_t smem_bytes(int N) {
         return sizeof(StepCoef<T>) * NB * (N / 2) + sizeof(T) * NB * KC * LDD + sizeof(cplx<T>) * KC * NB * BT +
-               sizeof(SeedPair) * NB;
+               sizeof(SeedPair) * NB + sizeof(size_t) * BT;
     }
 };
+
+// Asynchronous global -> shared copy of one complex value (8 or 16 bytes), so a
+// thread's loads of a chunk are all in flight together; cp_async_wait_all()
+// before the barrier that publishes them.
+template <typename C>
+__device__ __forceinline__ void cp_async_cplx(C* dst, const C* src) {
+    static_assert(sizeof(C) == 8 || sizeof(C) == 16, "complex64 or complex128");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;"
+                 ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src), "n"((int)sizeof(C)) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 template <typename T, int NB, int BT, int KC, int LW, int ML, int MB>
 __global__ void __launch_bounds__(FwdCfg<T, NB, BT, KC, LW, ML, MB>::THREADS)
@@ -79,9 +90,15 @@ contract_fwd(BandArgs a, const cplx<T>* __restrict__ F2, cplx<T>* __restrict__ c
     T* Dsm = reinterpret_cast<T*>(coef + NB * RS);                                 // [NB][KC][LDD]
     Cx* Fsm = reinterpret_cast<Cx*>(Dsm + NB * KC * LDD);                          // [KC][NB][BT]
     SeedPair* spair = reinterpret_cast<SeedPair*>(Fsm + KC * NB * BT);            // [NB] (FP32 seeds)
+    size_t* fbase = reinterpret_cast<size_t*>(spair + NB);                         // [BT] (m, n-block) of each function
     const int tid = threadIdx.x;
     constexpr bool F32 = std::is_same<T, float>::value;
     if (F32 && tid < NB) spair[tid] = make_seed_pair(a.lf2, tl.n2[tid], tl.m2);
+    constexpr size_t NOFN = ~(size_t)0;                                            // padding slot of the block
+    for (int b = tid; b < BT; b += THREADS) {
+        const int fb = bb * BT + b;
+        fbase[b] = fb < a.nfunc ? a.ws_off[a.fidx[fb]] + (size_t)tl.mi * N + tl.nb * NB : NOFN;
+    }
 
     // Step coefficients for rows r in [0, r_end - 1) of every pair.
     for (int idx = tid; idx < NB * (r_end - 1); idx += THREADS) {
@@ -146,20 +163,18 @@ contract_fwd(BandArgs a, const cplx<T>* __restrict__ F2, cplx<T>* __restrict__ c
             // ---- stage F2[k0 .. k0+KC) for the NB pairs and BT functions
             for (int idx = tid - NB * KC; idx < KC * BT; idx += THREADS - NB * KC) {
                 const int kk = idx % KC, b = idx / KC;
-                const int fb = bb * BT + b, k = k0 + kk;
-                Cx v[NB];
-                if (fb < a.nfunc && k < N) {
-                    const int f = a.fidx[fb];
-                    const Cx* src = F2 + a.ws_off[f] + ((size_t)k * 2 + tl.s) * N * N + (size_t)tl.mi * N + tl.nb * NB;
+                const int k = k0 + kk;
+                const size_t base = fbase[b];
+                if (base != NOFN && k < N) {
+                    const Cx* src = F2 + base + ((size_t)k * 2 + tl.s) * N * N;
 #pragma unroll
-                    for (int p = 0; p < NB; ++p) v[p] = src[p];
+                    for (int p = 0; p < NB; ++p) cp_async_cplx(&Fsm[(kk * NB + p) * BT + b], src + p);
                 } else {
 #pragma unroll
-                    for (int p = 0; p < NB; ++p) v[p] = mk<T>(T(0), T(0));
+                    for (int p = 0; p < NB; ++p) Fsm[(kk * NB + p) * BT + b] = mk<T>(T(0), T(0));
                 }
-#pragma unroll
-                for (int p = 0; p < NB; ++p) Fsm[(kk * NB + p) * BT + b] = v[p];
             }
+            cp_async_wait_all();
         }
         __syncthreads();
         if (active) {
