@@ -351,12 +351,17 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const __
                     }
                 }
                 dft_reg<R2, 1, float>(w);
-#pragma unroll
-                for (int q = 0; q < R2; ++q) Y[(ia + R1 * q) * W + jc] = (q == 0) ? w[0] : cmul(w[q], om[ia * q]);
                 dft_reg<R2, 1, float>(v);
-                // written back to the positions this thread read: no barrier needed before
+                // one twiddle load for both sectors; X written back to the positions
+                // this thread read: no barrier needed before
+                Y[ia * W + jc] = w[0];
+                X[ia * W + jc] = v[0];
 #pragma unroll
-                for (int q = 0; q < R2; ++q) X[(ia + R1 * q) * W + jc] = (q == 0) ? v[0] : cmul(v[q], om[ia * q]);
+                for (int q = 1; q < R2; ++q) {
+                    const float2 t = om[ia * q];
+                    Y[(ia + R1 * q) * W + jc] = cmul(w[q], t);
+                    X[(ia + R1 * q) * W + jc] = cmul(v[q], t);
+                }
                 fence_proxy_async_smem();   // before the slot is refilled by TMA
             }
             named_sync(1, CT);
