@@ -9,8 +9,11 @@
 //       (sector 1) -> intermediate rows I_s[p][j2] (128-byte segments).
 //   phase B, item (plane, s, pb): the 16 rows p in [16 pb, 16 pb + 16) of I_s
 //       (one 16 N x 8 B bulk copy) -> row DFTs over j2 with the pre-twist
-//       exp(i pi j2/N) for s = 1 -> sign (-1)^{n+m}, weight w_k/(2N^2) ->
-//       planes F2_s[mi][ni] (16 consecutive ni per row: 128-byte segments).
+//       exp(i pi j2/N) for s = 1 -> sign (-1)^{n+m}, weight w_k/(2N^2) -> a
+//       block of N rows mi x 16 consecutive ni of F2_s, staged in the item's
+//       slot and written to the planes by the producer warp with tensor stores
+//       (plain layout: 128-byte rows; tile-major: 32-byte rows) before it
+//       refills the slot.
 //
 // The intermediate lives in a ring of plane slots at the end of the workspace;
 // a B item discards the L2 lines it has read (discard.global.L2), so a slot's
@@ -30,7 +33,8 @@
 // N points); weight w_k/(4N^2); origin phase (-1)^n and i (-1)^{n0}.
 //
 // CTA layout: warps 0 .. CT/32-1 compute, one producer warp issues the loads
-// (after the dependency waits) into a two-slot ring (mbarriers full/empty), and
+// (after the dependency waits) into a two-slot ring (mbarriers full/empty) and
+// the B items' tensor stores, and
 // one signaller thread publishes the per-slot counters.  The compute warps hand
 // each finished phase to the signaller through a small record ring (mbarriers
 // sig_full/sig_empty); the signaller makes their global writes visible at GPU
