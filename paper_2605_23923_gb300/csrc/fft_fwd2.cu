@@ -72,7 +72,7 @@ struct Cfg {
     static constexpr int NR = 4;                        // signal records
     static constexpr int BOXR = N < 256 ? N : 256;      // rows per TMA box (at most 256)
     static constexpr size_t smem_bytes() {
-        return (size_t)NS * SLOTP * 8 + (size_t)YP * 8 + (size_t)N * 8 * 3 + (size_t)N * 4 + 2 * NS * 8 + 2 * NR * 8 +
+        return (size_t)NS * SLOTP * 8 + (size_t)YP * 8 + (size_t)N * 8 * 4 + (size_t)N * 4 + 2 * NS * 8 + 2 * NR * 8 +
                NS * 4 + NR * 4;
     }
     static constexpr int BLOCKS_PER_SM =
@@ -159,7 +159,8 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const __
     float2* om = Y + P::YP;                                    // exp(+2 pi i t/N)
     float2* tw = om + N;                                       // exp(+i pi t/N)
     float2* omq = tw + N;                                      // [q][ia] = om[ia * q] (B items: lanes vary ia)
-    float* wk = reinterpret_cast<float*>(omq + N);
+    float2* omq1 = omq + N;                                    // [q][ia] = e^{i pi ia (2q+1)/N} (B items, sector 1)
+    float* wk = reinterpret_cast<float*>(omq1 + N);
     uint64_t* full = reinterpret_cast<uint64_t*>(wk + N);      // [NS]
     uint64_t* empty = full + NS;                               // [NS]
     uint64_t* sig_full = empty + NS;                           // [NR]
@@ -178,6 +179,9 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const __
     for (int t = tid; t < N; t += blockDim.x) {
         om[t] = a.om32[t];
         omq[t] = a.om32[(t % R1) * (t / R1)];                  // t = q * R1 + ia, ia * q < N
+        const int u = (t % R1) * (2 * (t / R1) + 1);           // ia (2q + 1) < 2N
+        const float2 tu = a.twist32[u < N ? u : u - N];
+        omq1[t] = u < N ? tu : make_float2(-tu.x, -tu.y);
         tw[t] = a.twist32[t];
         wk[t] = a.w32[t];
     }
@@ -401,12 +405,21 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const __
 #pragma unroll
                 for (int q = 0; q < R2; ++q) v[q] = X[pl * N + ia + R1 * q];
                 if (it.s) {
+                    // pre-twist e^{i pi (ia + R1 q)/N} = e^{i pi q/R2} e^{i pi ia/N}: the first
+                    // factor is a constant per q, the second joins the inter-pass twiddle
 #pragma unroll
-                    for (int q = 0; q < R2; ++q) v[q] = cmul(v[q], tw[ia + R1 * q]);
+                    for (int q = 1; q < R2; ++q) {
+                        constexpr int S = 16 / R2;                 // e^{i pi q/R2} = omega_32^{S q}
+                        v[q] = cmul(v[q], make_float2(tw32_cos<float>(S * q), tw32_sin<float>(S * q)));
+                    }
+                    dft_reg<R2, 1, float>(v);
+#pragma unroll
+                    for (int q = 0; q < R2; ++q) v[q] = cmul(v[q], omq1[q * R1 + ia]);
+                } else {
+                    dft_reg<R2, 1, float>(v);
+#pragma unroll
+                    for (int q = 1; q < R2; ++q) v[q] = cmul(v[q], omq[q * R1 + ia]);
                 }
-                dft_reg<R2, 1, float>(v);
-#pragma unroll
-                for (int q = 1; q < R2; ++q) v[q] = cmul(v[q], omq[q * R1 + ia]);
 #pragma unroll
                 for (int q = 0; q < R2; ++q) Y[pl * P::PB + ia + R1 * q] = v[q];   // odd pitch: no conflicts
             }
