@@ -161,20 +161,42 @@ contract_fwd(BandArgs a, const cplx<T>* __restrict__ F2, cplx<T>* __restrict__ c
             }
         } else {
             // ---- stage F2[k0 .. k0+KC) for the NB pairs and BT functions
-            for (int idx = tid - NB * KC; idx < KC * BT; idx += THREADS - NB * KC) {
-                const int kk = idx % KC, b = idx / KC;
-                const int k = k0 + kk;
-                const size_t base = fbase[b];
-                if (base != NOFN && k < N) {
-                    const Cx* src = F2 + base + ((size_t)k * 2 + tl.s) * N * N;
+            if (tiles) {
+                // row-class launches (large batches): asynchronous copies, all in flight
+                for (int idx = tid - NB * KC; idx < KC * BT; idx += THREADS - NB * KC) {
+                    const int kk = idx % KC, b = idx / KC;
+                    const int k = k0 + kk;
+                    const size_t base = fbase[b];
+                    if (base != NOFN && k < N) {
+                        const Cx* src = F2 + base + ((size_t)k * 2 + tl.s) * N * N;
 #pragma unroll
-                    for (int p = 0; p < NB; ++p) cp_async_cplx(&Fsm[(kk * NB + p) * BT + b], src + p);
-                } else {
+                        for (int p = 0; p < NB; ++p) cp_async_cplx(&Fsm[(kk * NB + p) * BT + b], src + p);
+                    } else {
 #pragma unroll
-                    for (int p = 0; p < NB; ++p) Fsm[(kk * NB + p) * BT + b] = mk<T>(T(0), T(0));
+                        for (int p = 0; p < NB; ++p) Fsm[(kk * NB + p) * BT + b] = mk<T>(T(0), T(0));
+                    }
+                }
+                cp_async_wait_all();
+            } else {
+                // small batches: vector loads through registers (faster there, e.g. at
+                // N = 512 with 8 functions per block)
+                for (int idx = tid - NB * KC; idx < KC * BT; idx += THREADS - NB * KC) {
+                    const int kk = idx % KC, b = idx / KC;
+                    const int k = k0 + kk;
+                    const size_t base = fbase[b];
+                    Cx v[NB];
+                    if (base != NOFN && k < N) {
+                        const Cx* src = F2 + base + ((size_t)k * 2 + tl.s) * N * N;
+#pragma unroll
+                        for (int p = 0; p < NB; ++p) v[p] = src[p];
+                    } else {
+#pragma unroll
+                        for (int p = 0; p < NB; ++p) v[p] = mk<T>(T(0), T(0));
+                    }
+#pragma unroll
+                    for (int p = 0; p < NB; ++p) Fsm[(kk * NB + p) * BT + b] = v[p];
                 }
             }
-            cp_async_wait_all();
         }
         __syncthreads();
         if (active) {
