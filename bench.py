@@ -98,6 +98,36 @@ def num_coeffs(N):
     return N * (N + 1) * (2 * N + 1) // 6
 
 
+def measured_fp32_peak(torch, dev, stream):
+    """FP32 FMA throughput of this GPU, measured: cuBLAS SGEMM with TF32
+    disabled (FP32 fused multiply-adds on the CUDA cores), 8192^3, best of 10
+    launches timed with CUDA events.  Falls back to the nominal 152 SMs x 128
+    lanes x 2 flop x 2.07 GHz if the measurement fails."""
+    try:
+        old = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = False
+        n = 8192
+        a = torch.randn(n, n, device=dev, dtype=torch.float32)
+        b = torch.randn(n, n, device=dev, dtype=torch.float32)
+        c = torch.empty(n, n, device=dev, dtype=torch.float32)
+        for _ in range(3):
+            torch.matmul(a, b, out=c)
+        best = float("inf")
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            torch.matmul(a, b, out=c)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        torch.backends.cuda.matmul.allow_tf32 = old
+        del a, b, c
+        torch.cuda.empty_cache()
+        return 2.0 * n ** 3 / (best * 1e-3) / 1e12, "measured: cuBLAS SGEMM 8192^3, TF32 off, best of 10"
+    except Exception:      # noqa: BLE001 - report the nominal figure instead
+        return SMS * FP32_LANES * 2 * 2.07e9 / 1e12, "nominal: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -169,38 +199,25 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle timing (cpu_baseline and --impl reference)
 # ---------------------------------------------------------------------------
-ORACLE_ROW_STRIDE = 4
-
-
-def oracle_sample_seconds(f64grid):
-    """Seconds for one oracle forward at this N, from a bounded sample.
-
-    Stage 1 (torus DFT, both sectors) runs in full; stage 2 runs for every
-    ORACLE_ROW_STRIDE-th n row and is scaled by the stride.
-    """
-    from oracle import grid as G, transform as T
-    N = f64grid.shape[0]
-    t0 = time.perf_counter()
-    al, ga = G.alpha_nodes(N), G.gamma_nodes(N)
-    for sector in ("int", "half"):
-        idx = T.sector_indices(N, sector)
-        T.torus_dft(f64grid, idx, idx, al, ga)
-    t1 = time.perf_counter()
-    T.forward_separable(f64grid, row_stride=ORACLE_ROW_STRIDE)
-    t2 = time.perf_counter()
-    stage1 = t1 - t0
-    stage2_sample = max((t2 - t1) - stage1, 0.0)
-    return stage1 + stage2_sample * ORACLE_ROW_STRIDE, (t2 - t0)
+REF_ROW_STRIDE = 8      # --impl reference: per step, every 8th n row of each sector
 
 
 def cpu_baseline_for(f64grid):
-    est, spent = oracle_sample_seconds(f64grid)
-    return {"value": 1.0 / est, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": (f"one N={f64grid.shape[0]} function (function 0 of the batch): oracle stage 1 "
-                       f"(torus DFT, both sectors, numpy BLAS on up to {os.cpu_count()} threads) in full, "
-                       f"stage 2 (recurrence + theta contraction, single Python thread) on every "
-                       f"{ORACLE_ROW_STRIDE}th n row, scaled by {ORACLE_ROW_STRIDE}; {spent:.1f} s of CPU work"),
-            "seconds_per_fft": est}
+    """The FP64 oracle's forward of one grid, run in full on the host cores
+    (stage 1 and stage 2 of every (m, n) pair, the n rows spread over a pool
+    of spawned processes).  Returns the cpu_baseline object and the
+    coefficients (the reference for the error report)."""
+    from oracle import pool
+    cores = os.cpu_count() or 1
+    with pool.Runner(cores) as r:
+        t0 = time.perf_counter()
+        ref = r.forward_all(f64grid[None])[0]
+        sec = time.perf_counter() - t0
+    return ({"value": 1.0 / sec, "unit": UNIT, "cores": cores, "kind": "oracle",
+             "sample": (f"one whole N={f64grid.shape[0]} function (seeded white-noise grid, seed 2, rounded to "
+                        f"complex64): every coefficient, the n rows split over {cores} worker processes "
+                        f"(one BLAS thread each); {sec:.1f} s"),
+             "seconds_per_fft": sec, "estimated": False}, ref)
 
 
 def run_reference(args):
@@ -209,24 +226,33 @@ def run_reference(args):
     if rank != 0:
         return
     import su2inputs as I
+    from oracle import pool
     N = args.N
     rng = np.random.default_rng(2)
     f = I.draw_grid_gaussian((N, N, N), rng).astype(np.complex64).astype(np.complex128)
+    cores = os.cpu_count() or 1
     times = []
-    for i in range(args.warmup + args.steps):
-        est, _ = oracle_sample_seconds(f)
-        if i >= args.warmup:
-            times.append(est)
-    per_fft = statistics.mean(times)
+    with pool.Runner(cores) as r:
+        for i in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            r.forward_all(f[None], row_stride=REF_ROW_STRIDE)
+            if i >= args.warmup:
+                times.append(time.perf_counter() - t0)
+    step_s = statistics.mean(times)
+    per_fft = step_s * REF_ROW_STRIDE              # both stages scale with the rows computed
     value = 1.0 / per_fft
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_fft * args.batch * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": workload_name(N, args.batch), "N": N, "batch": args.batch},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": (f"per step: one N={N} function, oracle stage 1 in full, stage 2 on "
-                                        f"every {ORACLE_ROW_STRIDE}th n row scaled by {ORACLE_ROW_STRIDE}; "
-                                        f"value = FFTs/s of one host (the oracle is not batched)")},
+            "estimated": True,
+            "step_work": (f"one step = 1/{REF_ROW_STRIDE} of one N={N} function: stage 1 and stage 2 for every "
+                          f"{REF_ROW_STRIDE}th n row of each sector; ms_per_step is that measured time, value = "
+                          f"1 / ({REF_ROW_STRIDE} x seconds per step) FFTs/s, an extrapolation"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "estimated": True,
+                             "sample": (f"per step: one N={N} function (seeded white noise), every "
+                                        f"{REF_ROW_STRIDE}th n row of each sector, rows over {cores} worker "
+                                        f"processes; scaled by {REF_ROW_STRIDE}")},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -536,12 +562,33 @@ def main():
             dist.destroy_process_group()
         return
 
+    # ---- the FP64 oracle on the host cores (cpu_baseline), and the error of
+    # each arm against it: the oracle's grid (seeded white noise, rounded to
+    # complex64) goes into batch slot 0 of the timed launch configuration
+    cpu = err = None
+    if world == 1 and not args.no_cpu_baseline:
+        rng0 = np.random.default_rng(2)
+        f0 = I.draw_grid_gaussian((N, N, N), rng0).astype(np.complex64)
+        cpu, ref0 = cpu_baseline_for(f0.astype(np.complex128))
+        grid[:N ** 3].copy_(torch.from_numpy(f0.reshape(-1)))
+        ref_dev = torch.from_numpy(ref0).to(dev)
+        err = {"reference": "FP64 oracle (cpu_baseline run), every coefficient of one function in batch slot 0",
+               "metric": "max |gpu - oracle| / max |oracle| over the function's C(N) coefficients"}
+        for al in algos:
+            plans[al].forward(grid, out=outs[al], ws=ws, stream=stream)
+            plans[al].sync_status()
+            got = outs[al][:C].to(torch.complex128)
+            err[al] = float(((got - ref_dev).abs().max() / ref_dev.abs().max()).item())
+        del ref_dev
+
+    # ---- measured FP32 peak: cuBLAS SGEMM (TF32 off), 8192^3, best of 10
+    fp32_peak, fp32_src = measured_fp32_peak(torch, dev, stream)
+
     # ---- roofline of the dominant kernel
     peaks, peak_src = measured_peaks()
     fft_bytes = B * (8 * N ** 3 + 8 * (2 * N * N - 2 * N + 1) * N)
     contr_flops = B * 4 * N * C
     contr_bytes = B * (8 * (2 * N * N - 2 * N + 1) * N + 8 * C)
-    fp32_peak = SMS * FP32_LANES * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
 
     def stage_report(al):
         r = res[al]
@@ -558,7 +605,7 @@ def main():
                                    "alg_bytes": contr_bytes},
         }
         if al == "fp32":
-            out["stage2_contraction"].update(bound="alu", peak_tflops=fp32_peak,
+            out["stage2_contraction"].update(bound="alu", peak_tflops=fp32_peak, peak_source=fp32_src,
                                              frac=contr_flops / s2 / 1e12 / fp32_peak)
         else:
             out["stage2_contraction"].update(bound="hbm",
@@ -575,8 +622,7 @@ def main():
     elif algo == "fp32":
         ach = contr_flops / s2 / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
-                "traffic": None, "kernel": "stage-2 FP32 contraction (contract_fwd)",
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
+                "traffic": None, "kernel": "stage-2 FP32 contraction (contract_fwd)", "peak_source": fp32_src}
     else:
         ach = contr_bytes / s2 / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -589,11 +635,6 @@ def main():
         torch.cuda.empty_cache()
         extra = secondary_workloads(su2, I, torch, dev, stream, peaks, fp32_peak)
 
-    cpu = None
-    if world == 1 and not args.no_cpu_baseline:
-        rng0 = np.random.default_rng(2)
-        f0 = I.draw_grid_gaussian((N, N, N), rng0).astype(np.complex64).astype(np.complex128)
-        cpu = cpu_baseline_for(f0)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -607,6 +648,8 @@ def main():
         "stages": stages,
         "other_paths": others,
         "tc_vs_fp32_max_rel_diff": path_diff,
+        "max_rel_err_vs_oracle": err,
+        "fp32_peak": {"TFLOP/s": fp32_peak, "source": fp32_src},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": 2 * args.steps,  # stage-1 + stage-2 kernels per step (headline path; plus one

@@ -228,9 +228,16 @@ su2_status su2_backward(su2_plan_t plan, const void* grad_coeffs, void* grad_gri
  *  - No cudaMalloc / cudaFree or other allocation happens in this call; a plan
  *    created with SU2_FLAG_CUDA_GRAPH runs its kernels launch by launch here,
  *    since recording and instantiating a graph would allocate.
- *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) and caches it; make that first call before any
- *    stream capture.
+ *  - su2_plan (which allocates anyway) looks up the array's device address on
+ *    the plan's device (cudaGetSymbolAddress, which under CUDA's lazy module
+ *    loading loads the array onto the device) and caches it; this call only
+ *    reads that cache.
+ *  - Under lazy module loading (CUDA's default) the first launch of each
+ *    kernel in the process also loads that kernel's code onto the device.
+ *    Callers that may not allocate at all at transform time make one call with
+ *    the plan beforehand (this entry point or su2_forward), or run with
+ *    CUDA_MODULE_LOADING=EAGER, which loads everything when the context is
+ *    created.
  *  - All calls on a device share the one array and every call rewrites the
  *    part it reads (nothing needs to start at zero): calls whose kernels
  *    overlap on the GPU (other streams, or other host threads) race on it;

@@ -23,6 +23,8 @@ What it computes (all in float64 / complex128):
 * ``shifted``     -- the shifted Legendre polynomials A_r^L, B_r^L and the
                      divide-and-conquer projections of Sec. 4 (Theorem
                      "Divide-and-conquer"), used as identities in tests.
+* ``pool``        -- runs ``transform``'s row-restricted routines across the
+                     host cores (spawned processes) for large bandwidths.
 
 Parity status: every function here is pinned by tests in ``tests/`` against
 closed forms, library routines (scipy), exact rationals or invariants.

@@ -190,10 +190,14 @@ def _synthesis_planes(coeffs: np.ndarray, N: int, sector: str, row_weight) -> np
 
 
 def _torus_synthesis(G: np.ndarray, idx: np.ndarray, alpha, gamma) -> np.ndarray:
-    """sum_{n,m} G[k, n, m] e^{-i(n phi_j1 + m psi_j2)} -> f[j1, k, j2]."""
+    """sum_{n,m} G[k, n, m] e^{-i(n phi_j1 + m psi_j2)} -> f[j1, k, j2].
+
+    Two matrix products: the sum over n (t[j1, k, m]) and then the sum over m.
+    """
     En = np.exp(-1j * np.outer(alpha, idx / 2.0))        # [j1, n]
     Em = np.exp(-1j * np.outer(idx / 2.0, gamma))        # [m, j2]
-    t = np.einsum("an,knm->akm", En, G)
+    K, Nn, Nm = G.shape
+    t = (En @ np.transpose(G, (1, 0, 2)).reshape(Nn, K * Nm)).reshape(len(alpha), K, Nm)
     return t @ Em
 
 
@@ -256,3 +260,120 @@ def loss_and_grad(f: np.ndarray, target: np.ndarray, weights: str = "cc"):
     L = float(np.sum(wl * np.abs(r) ** 2))
     g = 2.0 * adjoint_separable(wl * r, N, weights)
     return L, g
+
+
+# ---------------------------------------------------------------------------
+# Row-restricted pieces: the same definitions evaluated for a subset of n, so
+# that large bandwidths can be split across host processes (tests only)
+# ---------------------------------------------------------------------------
+
+def forward_rows(fs: np.ndarray, n2_list, weights: str = "cc"):
+    """Coefficients f^(l)_{mn} of every pair whose n (doubled) is in n2_list,
+    for a batch of grids of one bandwidth on the periodic grid.
+
+    The definition of ``forward_separable`` restricted to those n: stage 1 is
+    the torus double sum for the listed n and every m of their sector (Sec. 6,
+    first-stage Proposition), as two matrix products; stage 2 the theta
+    contraction with conj(P^l_{nm}) = i^{n-m} d^l_{nm} from the recurrence
+    (Sec. 4, discrete Legendre transform), one d column per pair shared by
+    the batch.  fs: [B, N, N, N].  Returns (idx, vals): the packed indices of
+    the computed coefficients and vals[B, len(idx)].
+    """
+    fs = np.asarray(fs)
+    B, N = fs.shape[0], fs.shape[1]
+    al, be, ga, w, pref = _setup(N, weights, False)
+    idx_out, vals_out = [], []
+    for parity, sector in ((0, "int"), (1, "half")):
+        ns = np.array(sorted(n2 for n2 in n2_list if n2 % 2 == parity), dtype=np.int64)
+        if ns.size == 0:
+            continue
+        ms = sector_indices(N, sector)
+        jtop = _top_j(N, sector)
+        En = np.exp(1j * np.outer(ns / 2.0, al))             # [n, j1]
+        Em = np.exp(1j * np.outer(ms / 2.0, ga))             # [m, j2]
+        F2 = np.stack([((En @ fs[b].reshape(N, -1)).reshape(ns.size, N, N)) @ Em.T
+                       for b in range(B)])                   # [b, n, k, m]
+        for ni, n2 in enumerate(ns):
+            for mi, m2 in enumerate(ms):
+                j0, D = basis.wigner_d_column(int(n2), int(m2), be, jtop)
+                if D.shape[0] == 0:
+                    continue
+                s = w[None, :] * F2[:, ni, :, mi]                           # [b, k]
+                vals = pref * basis.i_pow((int(n2) - int(m2)) // 2) * (s @ D.T)   # [b, L]
+                idx_out.append(np.array([grid.coeff_index(j0 + 2 * i, int(m2), int(n2))
+                                         for i in range(D.shape[0])], dtype=np.int64))
+                vals_out.append(vals)
+    if not idx_out:
+        return np.zeros(0, dtype=np.int64), np.zeros((B, 0), dtype=np.complex128)
+    return np.concatenate(idx_out), np.concatenate(vals_out, axis=1)
+
+
+def synthesis_rows(cs: np.ndarray, N: int, n2_list, ks, modes=("synthesis",), weights: str = "cc"):
+    """Theta sums G[k, n, m] of the synthesis and/or the adjoint for the listed
+    n (doubled) at the beta nodes ks, for a batch of packed coefficient vectors.
+
+    Synthesis (Sec. 3, Peter-Weyl expansion):
+        G[k, n, m] = sum_l (2l+1) i^{m-n} d^l_{nm}(beta_k) c(l)_{mn};
+    adjoint of the forward quadrature map: (2l+1) replaced by pref * w_k.
+    The grid values follow as sum_{n,m} G[k, n, m] e^{-i(n alpha + m gamma)}
+    (``planes_from_rows``).  cs: [B, C]; modes: "synthesis" and/or "adjoint"
+    (the d columns are shared).  Returns {mode: {sector: (ns, G[B, K, n, m])}}.
+    """
+    cs = np.asarray(cs)
+    B = cs.shape[0]
+    ks = np.asarray(ks, dtype=np.int64)
+    be = grid.beta_nodes(N)[ks]
+    w = quadrature.weights(N, weights)[ks]
+    pref = _prefactor(N, False)
+    out = {mode: {} for mode in modes}
+    for parity, sector in ((0, "int"), (1, "half")):
+        ns = np.array(sorted(n2 for n2 in n2_list if n2 % 2 == parity), dtype=np.int64)
+        if ns.size == 0:
+            continue
+        ms = sector_indices(N, sector)
+        jtop = _top_j(N, sector)
+        G = {mode: np.zeros((B, ks.size, ns.size, ms.size), dtype=np.complex128) for mode in modes}
+        for ni, n2 in enumerate(ns):
+            for mi, m2 in enumerate(ms):
+                j0, D = basis.wigner_d_column(int(n2), int(m2), be, jtop)   # [L, K]
+                if D.shape[0] == 0:
+                    continue
+                js = j0 + 2 * np.arange(D.shape[0])
+                c = cs[:, [grid.coeff_index(int(j), int(m2), int(n2)) for j in js]]   # [B, L]
+                ph = basis.i_pow((int(m2) - int(n2)) // 2)
+                for mode in modes:
+                    if mode == "adjoint":
+                        t = (c @ D) * (pref * w)[None, :]
+                    elif mode == "synthesis":
+                        t = (c * (js + 1)[None, :].astype(np.float64)) @ D
+                    else:
+                        raise ValueError(mode)
+                    G[mode][:, :, ni, mi] = ph * t
+        for mode in modes:
+            out[mode][sector] = (ns, G[mode])
+    return out
+
+
+def planes_from_rows(parts, N: int) -> np.ndarray:
+    """Grid values f[b, j1, k, j2] at the beta nodes of ``synthesis_rows`` from
+    its outputs for disjoint n lists covering every n (summed over both
+    sectors): f = sum_{n,m} G[k, n, m] e^{-i(n alpha_j1 + m gamma_j2)}."""
+    al, ga = grid.alpha_nodes(N), grid.gamma_nodes(N)
+    f = None
+    for sector in ("int", "half"):
+        idx = sector_indices(N, sector)
+        pos = {int(n2): i for i, n2 in enumerate(idx)}
+        G = None
+        for part in parts:
+            if sector not in part:
+                continue
+            ns, g = part[sector]
+            if G is None:
+                G = np.zeros(g.shape[:2] + (idx.size, idx.size), dtype=np.complex128)
+            for i, n2 in enumerate(ns):
+                G[:, :, pos[int(n2)], :] += g[:, :, i, :]
+        if G is None:
+            continue
+        fs = np.stack([_torus_synthesis(G[b], idx, al, ga) for b in range(G.shape[0])])
+        f = fs if f is None else f + fs
+    return f

@@ -627,6 +627,8 @@ su2_status su2_plan(su2_plan_t* out, const su2_plan_desc* desc) {
     DeviceGuard g(desc->device);
     if (!g.ok) return SU2_ERR_CUDA;
 
+    // address of the allocation-free entry point's scratch array on this device
+    if (su2::noalloc_prepare(desc->device) != cudaSuccess) return SU2_ERR_CUDA;
     su2_plan_s* P = new (std::nothrow) su2_plan_s();
     if (!P) return SU2_ERR_OOM;
     P->device = desc->device;

@@ -12,9 +12,11 @@
 //
 // The array occupies SU2_NOALLOC_SCRATCH_BYTES on every GPU that loads this
 // library, for the lifetime of the process.  Host code cannot use the array's
-// name as a device address, so the device address is looked up once per device
-// with cudaGetSymbolAddress (done by the first call on that device, which
-// should therefore come before any stream capture) and cached.
+// name as a device address, so the device address is looked up with
+// cudaGetSymbolAddress, with the device current, and cached per device.  The
+// lookup is done by su2_plan (noalloc_prepare), not by the entry point: under
+// CUDA's lazy module loading it is what loads this file's module, array
+// included, onto the device, and plan creation allocates its tables anyway.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -32,26 +34,29 @@ std::atomic<void*> g_scratch_ptr[kMaxDevices];
 
 }  // namespace
 
+namespace su2 {
+cudaError_t noalloc_prepare(int device) {
+    if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+    if (g_scratch_ptr[device].load(std::memory_order_acquire)) return cudaSuccess;
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, su2_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    if (!p) return cudaErrorInvalidSymbol;
+    g_scratch_ptr[device].store(p, std::memory_order_release);
+    return cudaSuccess;
+}
+}  // namespace su2
+
 extern "C" su2_status su2_forward_noalloc(su2_plan_t plan, const void* grid, void* coeffs, void* cuda_stream) {
     if (!plan || !grid || !coeffs) return SU2_ERR_INVALID_ARG;
     size_t need = 0;
     su2_status s = su2_workspace_size(plan, &need);
     if (s != SU2_OK) return s;
     if (need > (size_t)SU2_NOALLOC_SCRATCH_BYTES) return SU2_ERR_WORKSPACE;
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess) return SU2_ERR_CUDA;
     const int plan_dev = su2::plan_device(plan);     // su2_forward runs on the plan's device
     if (plan_dev < 0 || plan_dev >= kMaxDevices) return SU2_ERR_CUDA;
     void* ptr = g_scratch_ptr[plan_dev].load(std::memory_order_acquire);
-    if (!ptr) {
-        if (plan_dev != dev && cudaSetDevice(plan_dev) != cudaSuccess) return SU2_ERR_CUDA;
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, su2_noalloc_scratch);
-        if (plan_dev != dev) cudaSetDevice(dev);
-        if (e != cudaSuccess || !p) return SU2_ERR_CUDA;
-        g_scratch_ptr[plan_dev].store(p, std::memory_order_release);
-        ptr = p;
-    }
+    if (!ptr) return SU2_ERR_CUDA;                   // su2_plan looked it up on this device
     // launch by launch even for SU2_FLAG_CUDA_GRAPH plans: recording and
     // instantiating a graph would allocate
     return (su2_status)su2::forward_direct(plan, grid, coeffs, ptr, cuda_stream);

@@ -59,5 +59,10 @@ int plan_device(const su2_plan_s* plan);
 // su2_forward's checks and launches, always enqueued launch by launch (never
 // recorded into a CUDA graph, whatever the plan's flags); returns an su2_status.
 int forward_direct(su2_plan_s* plan, const void* grid, void* coeffs, void* ws, void* stream);
+// Looks up, with `device` current, the device address of the allocation-free
+// entry point's scratch array and caches it for that device (the lookup loads
+// the module holding the array under lazy module loading, so it is done at
+// plan creation, which allocates anyway).  Idempotent.
+cudaError_t noalloc_prepare(int device);
 
 }  // namespace su2

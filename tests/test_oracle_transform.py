@@ -154,3 +154,48 @@ def test_finite_difference_gradient():
             d = (Lp - Lm) / (2 * h)
             fd.reshape(-1)[p] += d if part == 0 else 1j * d
     assert rel(fd, g) < 1e-7
+
+
+def _doubled_n(N):
+    return list(range(-(N - 1), N))
+
+
+@pytest.mark.parametrize("N", [4, 8])
+def test_forward_rows_equals_direct(N):
+    """Stage 2 split over disjoint lists of n (what the host-pool runner does)
+    reassembles the direct O(N^6) sum, for each grid of a batch."""
+    rng = np.random.default_rng(70 + N)
+    fs = np.stack([I.draw_grid_gaussian((N, N, N), rng) for _ in range(2)])
+    ns = _doubled_n(N)
+    out = np.zeros((2, grid.num_coeffs(N)), dtype=np.complex128)
+    seen = np.zeros(grid.num_coeffs(N), dtype=np.int64)
+    for part in (ns[0::3], ns[1::3], ns[2::3]):
+        idx, vals = T.forward_rows(fs, part)
+        out[:, idx] = vals
+        seen[idx] += 1
+    assert np.all(seen == 1)                      # every coefficient exactly once
+    for b in range(2):
+        assert rel(out[b], T.forward_direct(fs[b])) < 1e-13
+
+
+def test_synthesis_rows_equal_direct_and_transpose():
+    """Synthesis rows reassembled at a subset of beta nodes equal the direct
+    synthesis sum there; adjoint rows equal the brute-force conjugate
+    transpose of the direct forward matrix (N = 4)."""
+    N = 4
+    rng = np.random.default_rng(81)
+    cs = np.stack([I.draw_coeffs(N, rng) for _ in range(2)])
+    ks = [0, 2, 3]
+    ns = _doubled_n(N)
+    parts = [T.synthesis_rows(cs, N, part, ks, modes=("synthesis", "adjoint")) for part in (ns[:3], ns[3:])]
+    syn = T.planes_from_rows([p["synthesis"] for p in parts], N)
+    adj = T.planes_from_rows([p["adjoint"] for p in parts], N)
+    C = grid.num_coeffs(N)
+    A = np.zeros((C, N ** 3), dtype=np.complex128)
+    for p in range(N ** 3):
+        e = np.zeros(N ** 3, dtype=np.complex128)
+        e[p] = 1.0
+        A[:, p] = T.forward_direct(e.reshape(N, N, N))
+    for b in range(2):
+        assert rel(syn[b], T.inverse_direct(cs[b], N)[:, ks, :]) < 1e-12
+        assert rel(adj[b], (A.conj().T @ cs[b]).reshape(N, N, N)[:, ks, :]) < 1e-13
