@@ -124,8 +124,10 @@ fft_inv_two_phase(BandArgs a, const float2* __restrict__ ws, float2* __restrict_
                     const float2 g = Gs[(size_t)mi * N * N + (size_t)(ni >> 2) * 4 * N + (ni & 3)];
                     float sg = ((ni + mi) & 1) ? -1.f : 1.f;
                     if (s) sg = -sg;
-                    if (s == 0 && (ni == 0 || mi == 0)) sg = 0.f;
-                    v[q] = make_float2(g.x * sg, g.y * sg);
+                    // the integer sector's row and column 0 (Nyquist) are not part of the
+                    // transform; nothing writes them, so they are selected away, not scaled
+                    // by zero (whatever bits the workspace holds there, NaN included)
+                    v[q] = (s == 0 && (ni == 0 || mi == 0)) ? make_float2(0.f, 0.f) : make_float2(g.x * sg, g.y * sg);
                 }
                 dft_reg<R2, -1, float>(v);
 #pragma unroll
