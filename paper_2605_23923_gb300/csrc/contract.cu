@@ -392,6 +392,108 @@ contract_tr(BandArgs a, int mode, const cplx<T>* __restrict__ coeffs, cplx<T>* _
 }
 
 // ---------------------------------------------------------------------------
+// Float-float ("double-FP32") form of the recurrence, for the synthesis near
+// the poles.  There the three-term recurrence is badly conditioned (at x = 1
+// it adds two terms of size ~l to get d = 1), so the rounding of the FP32
+// state and of the FP32 step coefficients each leave errors of ~1e-5 to 1e-4
+// in d at l ~ 100 for nodes within a few steps of beta = 0 or pi; the forward
+// map does not see them (its weight w_k vanishes like sin beta there) but the
+// synthesis (weight 2l + 1 on the coefficients) does.  Carrying value and
+// coefficients as unevaluated sums hi + lo of two floats (products and sums
+// made exact with FMA-based two-product / two-sum) removes both.
+// ---------------------------------------------------------------------------
+struct FF { float h, l; };
+// a * b = p + e exactly
+__device__ __forceinline__ FF ff_two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, fmaf(a, b, -p)};
+}
+// a + b = s + e exactly (no ordering assumption)
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float z = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z))};
+}
+// renormalise (|h| >= |l| assumed)
+__device__ __forceinline__ FF ff_fast(float h, float l) {
+    const float s = __fadd_rn(h, l);
+    return {s, __fsub_rn(l, __fsub_rn(s, h))};
+}
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+    const FF p = ff_two_prod(a.h, b.h);
+    return ff_fast(p.h, fmaf(a.h, b.l, fmaf(a.l, b.h, p.l)));
+}
+__device__ __forceinline__ FF ff_sub(FF a, FF b) {
+    const FF s = ff_two_sum(a.h, -b.h);
+    return ff_fast(s.h, __fadd_rn(s.l, __fsub_rn(a.l, b.l)));
+}
+__device__ __forceinline__ FF ff_div(FF a, FF b) {
+    const float q = __fdiv_rn(a.h, b.h);
+    const float r = fmaf(-q, b.l, __fadd_rn(fmaf(-q, b.h, a.h), a.l));   // a - q b, to first order
+    return ff_fast(q, __fdiv_rn(r, b.h));
+}
+// sqrt of an integer p < 2^24 (exact in FP32)
+__device__ __forceinline__ FF ff_sqrt_int(float p) {
+    if (p <= 0.f) return {0.f, 0.f};
+    const float s = __fsqrt_rn(p);
+    return ff_fast(s, __fdiv_rn(fmaf(-s, s, p), __fmul_rn(2.f, s)));
+}
+
+// Step coefficients A, C of the pair (n2, m2) from 2l = J to J + 2 as
+// float-float (b keeps its hi/lo split of StepCoef).  All integers involved
+// are below 2^24 (J < 2^11).
+struct StepCoefFF { FF A, C; float bh, bl; };
+__device__ __forceinline__ StepCoefFF step_coef_ff(int J, int n2, int m2) {
+    StepCoefFF c;
+    const FF rs = ff_mul(ff_sqrt_int((float)((J + 2) * (J + 2) - n2 * n2)),
+                         ff_sqrt_int((float)((J + 2) * (J + 2) - m2 * m2)));
+    c.A = ff_div({(float)(2 * (J + 2) * (J + 1)), 0.f}, rs);
+    if (J == 0) {
+        c.C = {0.f, 0.f}; c.bh = 0.f; c.bl = 0.f;
+    } else {
+        const int ip0 = J * J - n2 * n2, iq0 = J * J - m2 * m2;
+        const FF r0 = ff_mul(ff_sqrt_int((float)(ip0 > 0 ? ip0 : 0)), ff_sqrt_int((float)(iq0 > 0 ? iq0 : 0)));
+        const FF t = ff_div(r0, rs);                                        // sqrt(p0 q0 / (p1 q1))
+        const FF u = ff_mul(t, {(float)(J + 2), 0.f});
+        c.C = ff_div(u, {(float)J, 0.f});
+        const float num = (float)(n2 * m2), den = (float)(J * (J + 2));
+        c.bh = num / den;
+        c.bl = fmaf(-c.bh, den, num) / den;
+    }
+    return c;
+}
+
+// Recurrence state in float-float with the same range extension as Rec<float>
+// (value = h * 2^(-120 E); while E > 0 the value is below 2^-39 and counts as 0).
+struct RecFF {
+    FF cur, prev;
+    float xh, xl;
+    int E;
+    __device__ __forceinline__ void seed32(const SeedPair& q, float4 tb, float2 xs, int k, int N) {
+        cur = {seed_value32(q, tb, k, N, E), 0.f};
+        prev = {0.f, 0.f};
+        xh = xs.x;
+        xl = xs.y;
+    }
+    __device__ __forceinline__ float value() const { return E == 0 ? cur.h : 0.f; }
+    __device__ __forceinline__ void step(const StepCoefFF& c) {
+        const FF xb = ff_sub({xh, xl}, {c.bh, c.bl});
+        const FF t = ff_mul(c.A, xb);
+        const FF nxt0 = ff_sub(ff_mul(t, cur), ff_mul(c.C, prev));
+        FF nxt = nxt0;
+        if (E > 0 && fabsf(nxt.h) >= 1.152921504606847e18f) {   // 2^60
+            const float sc = 7.52316384526264e-37f;               // 2^-120 (exact scaling)
+            nxt = {nxt.h * sc, nxt.l * sc};
+            cur = {cur.h * sc, cur.l * sc};
+            --E;
+        }
+        prev = cur;
+        cur = nxt;
+    }
+};
+
+
+// ---------------------------------------------------------------------------
 // Transposed contraction, complex64 (synthesis / adjoint), fused form.
 // A CTA owns a tile (sector, m, NB = 4 consecutive n) and BT = 8 functions;
 // thread (g, h) runs the recurrence chains of pairs 2h, 2h+1 at the two nodes
@@ -401,6 +503,10 @@ contract_tr(BandArgs a, int mode, const cplx<T>* __restrict__ coeffs, cplx<T>* _
 // range (one broadcast row per l).  No d values are stored.  Output: the
 // workspace planes tile-major, [s][mi][ni/4][k][ni%4], so that the two
 // threads of a node group write one 32-byte sector and a warp 512 bytes.
+// Synthesis at N >= 256: the warps whose 32 nodes lie within N/8 of a pole
+// run the recurrence in float-float (RecFF, coefficients with their low
+// parts); there the FP32 recurrence loses ~1e-4 of d at high l, which the
+// synthesis (weight 2l + 1, no sin(beta) factor) would show.
 // ---------------------------------------------------------------------------
 namespace tr32 {
 constexpr int NB = 4, BT = 8;
@@ -409,14 +515,19 @@ template <int N> struct Cfg {
     static constexpr int NODES = THREADS;                     // nodes per pass (2 per node group)
     static constexpr int PASSES = N / NODES;
     static constexpr int RS = N / 2;
+    static constexpr bool FF_POLES = N >= 256;                // float-float chains near the poles (synthesis)
     static constexpr size_t smem_bytes() {
-        return sizeof(StepCoef<float>) * NB * RS + sizeof(float2) * RS * NB * BT + sizeof(SeedPair) * NB + 16 * NB;
+        return sizeof(StepCoef<float>) * NB * RS + sizeof(float2) * RS * NB * BT + sizeof(SeedPair) * NB + 16 * NB +
+               (FF_POLES ? sizeof(float2) * NB * RS : 0);
     }
 };
 }  // namespace tr32
 
-template <int N>
-__global__ void __launch_bounds__(tr32::Cfg<N>::THREADS)
+// FF: instantiation for the synthesis at N >= 256 (float-float chains near the
+// poles); the adjoint and smaller N use the plain one, whose register count
+// stays unaffected.
+template <int N, bool FF>
+__global__ void __launch_bounds__(tr32::Cfg<N>::THREADS, FF ? 2 : 0)
 contract_tr32(BandArgs a, int mode, const float2* __restrict__ coeffs, float2* __restrict__ G) {
     using namespace tr32;
     using P = Cfg<N>;
@@ -431,12 +542,22 @@ contract_tr32(BandArgs a, int mode, const float2* __restrict__ coeffs, float2* _
     float2* Csm = reinterpret_cast<float2*>(coef + NB * RS);               // [RS][NB][BT]
     SeedPair* spair = reinterpret_cast<SeedPair*>(Csm + RS * NB * BT);      // [NB]
     int* rstart = reinterpret_cast<int*>(spair + NB);                       // [NB] first row of each pair
+    float2* coef_lo = reinterpret_cast<float2*>(rstart + NB);               // [NB][RS] (A, C) low parts
     const int tid = threadIdx.x;
+    constexpr bool ff = FF;
 
     for (int idx = tid; idx < NB * (L - 1); idx += P::THREADS) {
         const int p = idx % NB, r = idx / NB;
         const int J = tl.j0 + 2 * r;
-        if (J >= tl.mu2[p]) coef[p * RS + r] = step_coef<float>(J, tl.n2[p], tl.m2);
+        if (J >= tl.mu2[p]) {
+            if (ff) {
+                const StepCoefFF c = step_coef_ff(J, tl.n2[p], tl.m2);
+                coef[p * RS + r] = StepCoef<float>{c.A.h, c.C.h, c.bh, c.bl};
+                coef_lo[p * RS + r] = make_float2(c.A.l, c.C.l);
+            } else {
+                coef[p * RS + r] = step_coef<float>(J, tl.n2[p], tl.m2);
+            }
+        }
     }
     for (int idx = tid; idx < L * NB * BT; idx += P::THREADS) {
         const int b = idx % BT, p = (idx / BT) % NB, r = idx / (BT * NB);
@@ -467,6 +588,68 @@ contract_tr32(BandArgs a, int mode, const float2* __restrict__ coeffs, float2* _
 
     for (int pass = 0; pass < P::PASSES; ++pass) {
         const int ka = pass * P::NODES + 2 * gidx;           // nodes ka, ka + 1
+        // a warp's 32 nodes start at a multiple of 32: float-float chains when any
+        // of them is within N/8 of a pole
+        const int kw = pass * P::NODES + 32 * (tid >> 5);
+        if (ff && (kw < N / 8 || kw + 31 >= N - N / 8)) {     // compile-time false unless FF
+            RecFF ch[2][2];                                   // [node][pair]
+#pragma unroll
+            for (int nd = 0; nd < 2; ++nd) {
+                const int k = ka + nd;
+                ch[nd][0].seed32(q0, a.seed32[k], a.xsplit[k], k, N);
+                ch[nd][1].seed32(q1, a.seed32[k], a.xsplit[k], k, N);
+            }
+            float2 acc[2][2][BT];
+#pragma unroll
+            for (int nd = 0; nd < 2; ++nd)
+#pragma unroll
+                for (int pp = 0; pp < 2; ++pp)
+#pragma unroll
+                    for (int b = 0; b < BT; ++b) acc[nd][pp][b] = make_float2(0.f, 0.f);
+            for (int r = min(rs0, rs1); r < L; ++r) {
+                const float4* crow = reinterpret_cast<const float4*>(Csm + (r * NB + 2 * h) * BT);
+#pragma unroll
+                for (int pp = 0; pp < 2; ++pp) {
+                    if (r < (pp ? rs1 : rs0)) continue;
+                    float2 cv[BT];
+#pragma unroll
+                    for (int b2 = 0; b2 < BT / 2; ++b2) {
+                        const float4 t = crow[pp * (BT / 2) + b2];
+                        cv[2 * b2] = make_float2(t.x, t.y);
+                        cv[2 * b2 + 1] = make_float2(t.z, t.w);
+                    }
+                    const StepCoef<float> c32 = (pp ? c1p : c0p)[r];
+                    const float2 clo = coef_lo[(2 * h + pp) * RS + r];
+                    const StepCoefFF cf{{c32.A, clo.x}, {c32.C, clo.y}, c32.bh, c32.bl};
+#pragma unroll
+                    for (int nd = 0; nd < 2; ++nd) {
+                        RecFF& rc = ch[nd][pp];
+                        const float dv = rc.value();
+#pragma unroll
+                        for (int b = 0; b < BT; ++b) {
+                            acc[nd][pp][b].x = fmaf(dv, cv[b].x, acc[nd][pp][b].x);
+                            acc[nd][pp][b].y = fmaf(dv, cv[b].y, acc[nd][pp][b].y);
+                        }
+                        if (r + 1 < L) rc.step(cf);
+                    }
+                }
+            }
+#pragma unroll
+            for (int nd = 0; nd < 2; ++nd) {
+                const int k = ka + nd;
+#pragma unroll
+                for (int b = 0; b < BT; ++b) {
+                    const int fb = bb * BT + b;
+                    if (fb >= a.nfunc) continue;
+                    const int f = a.fidx[fb];
+                    float4* dst = reinterpret_cast<float4*>(G + a.ws_off[f] + (size_t)tl.s * N * N * N +
+                                                            (size_t)tl.mi * N * N + (size_t)(ni0 >> 2) * 4 * N +
+                                                            (size_t)4 * k + (ni0 & 3));
+                    *dst = make_float4(acc[nd][0][b].x, acc[nd][0][b].y, acc[nd][1][b].x, acc[nd][1][b].y);
+                }
+            }
+            continue;
+        }
         Rec<float> ch[2][2];                                  // [node][pair]
 #pragma unroll
         for (int nd = 0; nd < 2; ++nd) {
@@ -592,7 +775,7 @@ static cudaError_t launch_tr_t(const BandArgs& a, int mode, const void* coeffs, 
 template <int N>
 static cudaError_t launch_tr32_n(const BandArgs& a, int mode, const void* coeffs, void* ws, cudaStream_t st) {
     using P = tr32::Cfg<N>;
-    auto kern = contract_tr32<N>;
+    auto kern = (P::FF_POLES && mode == 0) ? contract_tr32<N, P::FF_POLES> : contract_tr32<N, false>;
     const size_t smem = P::smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

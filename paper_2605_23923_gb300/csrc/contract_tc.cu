@@ -13,15 +13,21 @@
 //
 // One persistent CTA per SM owns tiles of 4 consecutive n at fixed
 // (sector, m) and 64 functions.  Warp roles, connected by mbarriers:
-//   warp 0      TMA: F2 chunk [64 functions][16 nodes][4 n] into a staging ring
-//               (the planes are tile-major, so a function's chunk is 512 B)
+//   warp 0      TMA: F2 chunk [64 functions][16 nodes][4 n] into a ring of four
+//               stages (the planes are tile-major, so a function's chunk is 512 B)
 //   warp 1      MMA issue (one thread), tensor-memory owner
-//   warps 2-5, 10-11  convert staged F2 (fp32) to the BF16 hi/lo A operands
+//   warps 2-5, 10-11  convert a landed F2 chunk (fp32) into the BF16 hi/lo A
+//               operands in place: all of it is read into registers, the six
+//               warps meet at a named barrier, then the operands are written
+//               over the same 32 KB (hi and lo of 4 pairs fill it exactly)
 //   warps 6-9   two generator groups (even / odd chunks): the d-values of the
 //               4 pairs x 16 nodes by the three-term recurrence, written as the
 //               BF16 hi/lo B operands
 //   warps 12-15 epilogue: tensor memory -> i^{n-m} * coefficients
-// Two stages of staging / A / B; the MMA commit of a stage frees it.
+// Four stages of F2 / A (a stage is reloaded once the MMAs that read it are
+// done), two of B; the MMA commits free them.  With the operands converted in
+// place the TMA can run up to three chunks (96 KB) ahead of the MMAs, which
+// covers the DRAM latency at this kernel's share of the bandwidth.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -46,23 +52,27 @@ constexpr int NMAX = 256;
 // Operand layouts (SWIZZLE_NONE canonical; core matrix = 8 rows x 16 bytes):
 // A, K-major:  (row, kk) -> (row/8)*SBO_A + (kk/8)*LBO_A + (row%8)*16 + (kk%8)*2
 // B, MN-major: (kk, col) -> (col/8)*SBO_B + (kk/8)*LBO_B + (kk%8)*16 + (col%8)*2
-// LBO_A = 144 (not 128) and a 32-byte skew between the pairs' A buffers keep
-// the converters' 4-byte stores free of bank conflicts.
-constexpr int LBO_A = 144, SBO_A = 288, LBO_B = 128, SBO_B = 256;
-constexpr int OPA = 16 * SBO_A + 32;        // one pair's A matrix (hi or lo), skewed
+// A: the 16 row groups of one K half are contiguous (SBO_A = 128) and the
+// second K half follows 16 bytes later than dense (LBO_A = 2064); with a
+// 16-byte skew between the eight matrices (OPA) the converters' 8-byte stores
+// of one batch row hit 32 different banks, and the eight matrices of a stage
+// (33,024 bytes) fit over the 32 KB of staged F2 they are converted from.
+constexpr int LBO_A = 2064, SBO_A = 128, LBO_B = 128, SBO_B = 256;
+constexpr int OPA = LBO_A + 16 * SBO_A + 16;  // one pair's A matrix (hi or lo), skewed
 constexpr int OPB = 16 * SBO_B;             // one pair's B matrix (hi or lo)
 constexpr int STAGE_BYTES = BM * KC * NP * 8;       // fp32 staging: 32 KB
 constexpr int A_BYTES = 2 * NP * OPA;
+constexpr int NSA = 4;                      // F2 / A stages
+constexpr int SA = ((A_BYTES > STAGE_BYTES ? A_BYTES : STAGE_BYTES) + 127) / 128 * 128;
 constexpr int B_BYTES = 2 * NP * OPB;
-constexpr int OFF_STG = 0;
-constexpr int OFF_A = OFF_STG + 2 * STAGE_BYTES;
-constexpr int OFF_B = OFF_A + ((2 * A_BYTES + 127) / 128) * 128;
+constexpr int OFF_STG = 0;                  // stage st at OFF_STG + st * SA (F2, then its A operands)
+constexpr int OFF_B = OFF_STG + NSA * SA;
 constexpr int OFF_COEF = OFF_B + 2 * B_BYTES;
 constexpr int OFF_TAB = OFF_COEF + 2 * NP * RMAX * (int)sizeof(StepCoef<float>);
 // seed32 (float4) + lf2 (double) + xsplit (float2) + seed parameters of the pairs
 constexpr int TAB_BYTES = NMAX * 16 + NMAX * 8 + NMAX * 8 + 2 * NP * (int)sizeof(SeedPair) + NMAX * 4;
 constexpr int OFF_BAR = OFF_TAB + TAB_BYTES;
-constexpr int NBAR = 14;
+constexpr int NBAR = 4 * NSA + 2 * 2 + 4;
 constexpr int SMEM_BYTES = OFF_BAR + NBAR * 8 + 16;
 static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 constexpr uint32_t TMEM_COLS = 512;         // 4 pairs x 128 columns, or two halves of 4 x 64
@@ -154,13 +164,13 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
     constexpr int NCH = N / KC;
     static_assert(NCH % 2 == 0, "even number of chunks: a generator group keeps its stage");
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OFF_BAR);
-    uint64_t* bar_full = bars + 0;     // [2] TMA landed                 (count 1 + tx)
-    uint64_t* bar_sfree = bars + 2;    // [2] staging consumed            (count N_CONV)
-    uint64_t* bar_afull = bars + 4;    // [2] A operands written          (count N_CONV)
-    uint64_t* bar_bfull = bars + 6;    // [2] B operands written          (count 2)
-    uint64_t* bar_opfree = bars + 8;   // [2] MMAs of the stage done      (tcgen05.commit)
-    uint64_t* bar_accfull = bars + 10; // [2] accumulators of a tile in half h final (tcgen05.commit)
-    uint64_t* bar_hfree = bars + 12;   // [2] epilogue drained half h      (count 4)
+    uint64_t* bar_full = bars + 0;               // [NSA] TMA landed              (count 1 + tx)
+    uint64_t* bar_afull = bars + NSA;            // [NSA] A operands written      (count N_CONV)
+    uint64_t* bar_opa = bars + 2 * NSA;          // [NSA] MMAs of the A stage done (tcgen05.commit)
+    uint64_t* bar_bfull = bars + 3 * NSA;        // [2] B operands written        (count 2)
+    uint64_t* bar_opb = bars + 3 * NSA + 2;      // [2] MMAs of the B stage done  (tcgen05.commit)
+    uint64_t* bar_accfull = bars + 3 * NSA + 4;  // [2] accumulators of a tile in half h final (tcgen05.commit)
+    uint64_t* bar_hfree = bars + 3 * NSA + 6;    // [2] epilogue drained half h    (count 4)
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + NBAR);
     float4* t_seed = reinterpret_cast<float4*>(smem + OFF_TAB);
     double* t_lf2 = reinterpret_cast<double*>(t_seed + NMAX);
@@ -181,12 +191,14 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < NSA; ++i) {
             mbar_init(&bar_full[i], 1);
-            mbar_init(&bar_sfree[i], N_CONV);
             mbar_init(&bar_afull[i], N_CONV);
+            mbar_init(&bar_opa[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
             mbar_init(&bar_bfull[i], 2);
-            mbar_init(&bar_opfree[i], 1);
+            mbar_init(&bar_opb[i], 1);
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&bar_accfull[i], 1);
@@ -216,11 +228,11 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
                 if (!tl.any) continue;
                 const int bb = item % nbb;
                 for (int c = 0; c < NCH; ++c, ++g) {
-                    const int st = g & 1;
-                    const uint32_t u = g >> 1;
-                    if (u > 0) mbar_wait_bounded(&bar_sfree[st], (u - 1) & 1, a.err);
+                    const int st = g % NSA;
+                    const uint32_t u = g / NSA;
+                    if (u > 0) mbar_wait_bounded(&bar_opa[st], (u - 1) & 1, a.err);   // its A operands read
                     mbar_arrive_expect_tx(&bar_full[st], (uint32_t)STAGE_BYTES);
-                    tma_load_5d(smem + OFF_STG + st * STAGE_BYTES, &tmap, c * KC * NP, tl.nb, tl.mi, tl.s, bb * BM,
+                    tma_load_5d(smem + OFF_STG + st * SA, &tmap, c * KC * NP, tl.nb, tl.mi, tl.s, bb * BM,
                                 &bar_full[st], pol);
                 }
             }
@@ -249,13 +261,12 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
                 const uint32_t pstride = big ? 128u : 64u;
                 tc_fence_after();
                 for (int c = 0; c < NCH; ++c, ++g) {
-                    const int st = g & 1;
-                    const uint32_t u = g >> 1;
-                    mbar_wait_bounded(&bar_afull[st], u & 1, a.err);
-                    mbar_wait_bounded(&bar_bfull[st], u & 1, a.err);
+                    const int sa = g % NSA, sb = g & 1;
+                    mbar_wait_bounded(&bar_afull[sa], (g / NSA) & 1, a.err);
+                    mbar_wait_bounded(&bar_bfull[sb], (g >> 1) & 1, a.err);
                     tc_fence_after();
-                    unsigned char* Ab = smem + OFF_A + st * A_BYTES;
-                    unsigned char* Bb = smem + OFF_B + st * B_BYTES;
+                    unsigned char* Ab = smem + OFF_STG + sa * SA;
+                    unsigned char* Bb = smem + OFF_B + sb * B_BYTES;
 #pragma unroll
                     for (int p = 0; p < NP; ++p) {
                         if (!tl.valid[p]) continue;
@@ -268,7 +279,8 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
                         mma_bf16(d, ah, bl, idesc, true);
                         mma_bf16(d, al, bh, idesc, true);
                     }
-                    mma_commit(&bar_opfree[st]);
+                    mma_commit(&bar_opa[sa]);
+                    mma_commit(&bar_opb[sb]);
                 }
                 mma_commit(&bar_accfull[h0]);
             }
@@ -282,40 +294,51 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
         // the stores are 8 bytes; the generators write the d-values in the same order.
         const int cw = (warp < W_CONV + 4) ? warp - W_CONV : 4 + (warp - W_CONV2);
         const int ct = cw * 32 + lane;                     // 0 .. 191
+        constexpr int NIT = BM * (KC / 4) * NP;            // 1024 items per chunk
+        constexpr int MAXI = (NIT + 32 * N_CONV - 1) / (32 * N_CONV);
         uint32_t g = 0;
         for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
             Tile<NP> tl;
             tl.decode(N, item / nbb);
             if (!tl.any) continue;
             for (int c = 0; c < NCH; ++c, ++g) {
-                const int st = g & 1;
-                const uint32_t u = g >> 1;
-                mbar_wait_bounded(&bar_full[st], u & 1, a.err);
-                if (u > 0) mbar_wait_bounded(&bar_opfree[st], (u - 1) & 1, a.err);
-                const float2* stg = reinterpret_cast<const float2*>(smem + OFF_STG + st * STAGE_BYTES);
-                unsigned char* Ab = smem + OFF_A + st * A_BYTES;
-                for (int i = ct; i < BM * (KC / 4) * NP; i += 32 * N_CONV) {
-                    const int p = i & 3, t = (i >> 2) & 3, b = i >> 4;
-                    float2 v[4];
+                const int st = g % NSA;
+                mbar_wait_bounded(&bar_full[st], (g / NSA) & 1, a.err);   // stage free: TMA waited for the MMAs
+                const float2* stg = reinterpret_cast<const float2*>(smem + OFF_STG + st * SA);
+                unsigned char* Ab = smem + OFF_STG + st * SA;
+                // every converter reads its items of the staged chunk before any of
+                // them overwrites the chunk with the operands
+                float2 v[MAXI][4];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) v[q] = stg[(b * KC + t + 4 * q) * NP + p];
-                    uint2 hr, lr, hi_, li;
-                    split2(v[0].x, v[1].x, hr.x, lr.x);
-                    split2(v[2].x, v[3].x, hr.y, lr.y);
-                    split2(v[0].y, v[1].y, hi_.x, li.x);
-                    split2(v[2].y, v[3].y, hi_.y, li.y);
-                    const int ore = a_off(2 * b, 4 * t), oim = a_off(2 * b + 1, 4 * t);
-                    *reinterpret_cast<uint2*>(Ab + p * OPA + ore) = hr;
-                    *reinterpret_cast<uint2*>(Ab + p * OPA + oim) = hi_;
-                    *reinterpret_cast<uint2*>(Ab + (NP + p) * OPA + ore) = lr;
-                    *reinterpret_cast<uint2*>(Ab + (NP + p) * OPA + oim) = li;
+                for (int j = 0; j < MAXI; ++j) {
+                    const int i = ct + 32 * N_CONV * j;
+                    if (i < NIT) {
+                        const int p = i & 3, t = (i >> 2) & 3, b = i >> 4;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) v[j][q] = stg[(b * KC + t + 4 * q) * NP + p];
+                    }
+                }
+                named_sync(3, 32 * N_CONV);
+#pragma unroll
+                for (int j = 0; j < MAXI; ++j) {
+                    const int i = ct + 32 * N_CONV * j;
+                    if (i < NIT) {
+                        const int p = i & 3, t = (i >> 2) & 3, b = i >> 4;
+                        uint2 hr, lr, hi_, li;
+                        split2(v[j][0].x, v[j][1].x, hr.x, lr.x);
+                        split2(v[j][2].x, v[j][3].x, hr.y, lr.y);
+                        split2(v[j][0].y, v[j][1].y, hi_.x, li.x);
+                        split2(v[j][2].y, v[j][3].y, hi_.y, li.y);
+                        const int ore = a_off(2 * b, 4 * t), oim = a_off(2 * b + 1, 4 * t);
+                        *reinterpret_cast<uint2*>(Ab + p * OPA + ore) = hr;
+                        *reinterpret_cast<uint2*>(Ab + p * OPA + oim) = hi_;
+                        *reinterpret_cast<uint2*>(Ab + (NP + p) * OPA + ore) = lr;
+                        *reinterpret_cast<uint2*>(Ab + (NP + p) * OPA + oim) = li;
+                    }
                 }
                 fence_proxy_async_smem();
                 __syncwarp();
-                if (lane == 0) {
-                    mbar_arrive(&bar_sfree[st]);
-                    mbar_arrive(&bar_afull[st]);
-                }
+                if (lane == 0) mbar_arrive(&bar_afull[st]);
             }
         }
     } else if (warp >= W_GEN && warp < W_GEN + 4) {
@@ -355,7 +378,7 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
                 const int st = g & 1;
                 if (st != grp) continue;
                 const uint32_t u = g >> 1;
-                if (u > 0) mbar_wait_bounded(&bar_opfree[st], (u - 1) & 1, a.err);
+                if (u > 0) mbar_wait_bounded(&bar_opb[st], (u - 1) & 1, a.err);
                 unsigned char* Bh = smem + OFF_B + st * B_BYTES + p * OPB + (kk >> 3) * LBO_B + (kk & 7) * 16;
                 unsigned char* Bl = Bh + NP * OPB;
                 const int k = c * KC + ((kk >> 2) | ((kk & 3) << 2));   // node at K position kk
