@@ -48,6 +48,7 @@ struct Band {
     bool literal = false;         // grids on the printed grid (forward only)
     float2* d_lit_w = nullptr;
     float2* d_lit_twist = nullptr;
+    float2* d_lit_bs = nullptr;
     int s1_two_phase = 0;         // kernel choices (defaults, or the autotuner's)
     int s2_bt = 0;
     int* d_s2_tiles = nullptr;    // FP32 contraction tiles grouped by rows of l (see BandArgs)
@@ -251,7 +252,12 @@ cudaError_t build_band(su2_plan_s* P, Band& b) {
     if ((e = P->upload(&b.d_om64, om64.data(), N)) != cudaSuccess) return e;
     if ((e = P->upload(&b.d_twist32, tw32.data(), N)) != cudaSuccess) return e;
     if ((e = P->upload(&b.d_twist64, tw64.data(), N)) != cudaSuccess) return e;
-    if (b.literal) {
+    if (b.literal && su2::fft_literal_bluestein(N)) {
+        // chirps, chirp filter spectrum and twiddles of the Bluestein DFTs
+        std::vector<float2> bs;
+        su2::fft_literal_bluestein_tables(N, bs);
+        if ((e = P->upload(&b.d_lit_bs, bs.data(), bs.size())) != cudaSuccess) return e;
+    } else if (b.literal) {
         // (N-1)-point DFT matrix at the output frequencies r - N/2 and the half-bin twist
         const int M = N - 1;
         std::vector<float2> W((size_t)N * N), lt(2 * N);
@@ -304,6 +310,7 @@ su2::BandArgs band_args(const su2_plan_s* P, const Band& b) {
     a.literal = b.literal ? 1 : 0;
     a.lit_w = b.d_lit_w;
     a.lit_twist = b.d_lit_twist;
+    a.lit_bs = b.d_lit_bs;
     a.s2_tiles = b.d_s2_tiles;
     for (int c = 0; c < 3; ++c) a.s2_ntiles[c] = b.s2_ntiles[c];
     const size_t n3 = (b.full_group ? 2 : 1) * (size_t)b.N * b.N * b.N;   // elements of one grid

@@ -205,6 +205,7 @@ template <> struct Radix<64>  { static constexpr int R1 = 8,  R2 = 8; };
 template <> struct Radix<128> { static constexpr int R1 = 16, R2 = 8; };
 template <> struct Radix<256> { static constexpr int R1 = 16, R2 = 16; };
 template <> struct Radix<512> { static constexpr int R1 = 32, R2 = 16; };
+template <> struct Radix<1024> { static constexpr int R1 = 32, R2 = 32; };
 
 // ---------------------------------------------------------------------------
 // Thread-block cluster helpers (distributed shared memory).
@@ -371,6 +372,8 @@ struct BandArgs {
                                   // aux_ring then counts the literal kernel's CTAs (one N^2 slab each)
     const float2* lit_w;          // [N][N] e^{2 pi i (r - N/2) t/(N-1)}, column N-1 zero (literal grid)
     const float2* lit_twist;      // [2N] e^{i pi u/(N-1)} (literal grid)
+    const float2* lit_bs;         // literal grid, N >= 64: Bluestein tables (chirps, filter, twiddles;
+                                  // layout in fft_literal.cu); aux_ring then counts planes per chunk
     const int* s2_tiles;          // FP32 contraction tiles by rows of l: L <= 32, then 32 < L <= 64,
                                   // then L > 64, concatenated (tile numbers as Tile<4>::decode takes)
     int s2_ntiles[3];             // tiles in each of those classes

@@ -17,12 +17,30 @@
 // as on the periodic grid.  Output F2_s[k][m][n] = w_k/(2M^2) * phase * Y[n][m];
 // the integer sector's row and column of index 0 (m or n = -N/2) stay zero.
 //
-// Kernel: persistent CTAs, one plane (function, k, s) at a time; both products
-// are complex FP32 GEMMs on the CUDA cores, 64 x 64 output blocks, 256 threads
-// with 4 x 4 complex accumulators each, operand chunks of 16 staged in shared
-// memory with the next chunk prefetched into registers.  T goes to a per-CTA
-// slab of the workspace (N^2 complex; read back at once, so it stays in L2).
+// N >= 64 (M = 63, 127, 255, 511): each M-point DFT is taken by Bluestein's
+// chirp-z identity, q t = (q^2 + t^2 - (q - t)^2)/2, so
+//   sum_t x_t w^{q t} = e^{i pi q^2/M} sum_t (x_t e^{i pi t^2/M}) e^{-i pi (q - t)^2/M},
+// w = e^{2 pi i/M}: a convolution with the chirp e^{-i pi u^2/M}, taken
+// cyclically with length L = 2N (the N outputs q = -N/2 .. N/2 - 1 from M
+// inputs touch u in a range of 2N - 2 < L values, so nothing wraps) by two
+// L-point FFTs and the filter's spectrum, precomputed in FP64 on the host.
+// Launch 1 (rows): per plane, 16 rows j1 (folded), both sectors, convolution
+// over j2 -> T_s[j1][c] in a chunk buffer of the workspace (sized to stay in
+// L2); launch 2 (columns): 16 columns c of T_s, convolution over j1, scale,
+// phase, planes.  Sector 1's twist e^{i pi (j1 + j2)/M} splits into the two
+// launches' input chirps, e^{i pi (t^2 + t)/M}.  O(N^3 log N) per function,
+// like the periodic grid.
+//
+// N < 64, dense products: persistent CTAs, one plane (function, k, s) at a
+// time; both products are complex FP32 GEMMs on the CUDA cores, 64 x 64
+// output blocks, 256 threads with 4 x 4 complex accumulators each, operand
+// chunks of 16 staged in shared memory with the next chunk prefetched into
+// registers.  T goes to a per-CTA slab of the workspace (N^2 complex; read
+// back at once, so it stays in L2).
 #include <cuda_runtime.h>
+#include <math.h>
+
+#include <vector>
 
 #include "common.cuh"
 #include "su2_internal.h"
@@ -211,7 +229,276 @@ fft_fwd_literal(BandArgs a, const float2* __restrict__ grid, float2* __restrict_
 
 }  // namespace lit
 
+// ---------------------------------------------------------------------------
+// Bluestein (chirp-z) form, N >= 64
+// ---------------------------------------------------------------------------
+namespace litbs {
+
+// Table block (float2 each): chirp_in[2][N] (sector 0: e^{i pi t^2/M}; sector 1:
+// e^{i pi (t^2 + t)/M}), chirp_out[N] (e^{i pi q^2/M}, q = c - N/2), filter[L]
+// (FFT of the chirp e^{-i pi u^2/M} over one period of L, divided by L, stored in
+// the order the forward four-step FFT leaves its output), om[L] (e^{2 pi i t/L}).
+template <int N> struct Cfg {
+    static constexpr int M = N - 1, L = 2 * N;
+    static constexpr int R1 = Radix<L>::R1, R2 = Radix<L>::R2;
+    static constexpr int ROWS = N >= 512 ? 8 : 16;       // rows (launch 1) / columns (launch 2) per item
+    static constexpr int PITCH = L + L / R1;             // one pad element per R1 block
+    static constexpr int THREADS = 256;
+    static constexpr int TAB = 3 * N + 2 * L;
+    static constexpr size_t smem_bytes() { return (size_t)ROWS * PITCH * 8 + (size_t)ROWS * N * 8 + (size_t)TAB * 8; }
+    __host__ __device__ static constexpr int pad(int p) { return p + p / R1; }
+};
+
+// Cyclic convolution of each of the ROWS rows of buf (length L, padded) with
+// the chirp: forward four-step FFT (R2-point DFTs over stride R1, twiddle,
+// R1-point DFTs), filter, and the transposed steps backwards (inverse R1-point
+// DFTs, conjugate twiddle, inverse R2-point DFTs), so the permuted frequency
+// order of the forward FFT is never undone explicitly.
+template <int N>
+__device__ __forceinline__ void conv_rows(float2* buf, const float2* __restrict__ filt, const float2* __restrict__ om) {
+    using P = Cfg<N>;
+    constexpr int R1 = P::R1, R2 = P::R2;
+    const int tid = threadIdx.x;
+    for (int task = tid; task < P::ROWS * R1; task += P::THREADS) {
+        const int row = task / R1, ia = task % R1;
+        float2* x = buf + row * P::PITCH;
+        float2 v[R2];
+#pragma unroll
+        for (int q = 0; q < R2; ++q) v[q] = x[P::pad(ia + R1 * q)];
+        dft_reg<R2, -1, float>(v);
+#pragma unroll
+        for (int qq = 1; qq < R2; ++qq) v[qq] = cmul(v[qq], cconj(om[ia * qq]));
+#pragma unroll
+        for (int qq = 0; qq < R2; ++qq) x[P::pad(ia + R1 * qq)] = v[qq];
+    }
+    __syncthreads();
+    for (int task = tid; task < P::ROWS * R2; task += P::THREADS) {
+        const int row = task / R2, qq = task % R2;
+        float2* x = buf + row * P::PITCH + qq * (R1 + 1);  // pad(qq R1 + ia) = qq (R1 + 1) + ia
+        float2 v[R1];
+#pragma unroll
+        for (int ia = 0; ia < R1; ++ia) v[ia] = x[ia];
+        dft_reg<R1, -1, float>(v);                       // v[qa]: frequency qq + R2 qa
+#pragma unroll
+        for (int qa = 0; qa < R1; ++qa) v[qa] = cmul(v[qa], filt[qa + R1 * qq]);
+        dft_reg<R1, 1, float>(v);
+#pragma unroll
+        for (int ia = 1; ia < R1; ++ia) v[ia] = cmul(v[ia], om[ia * qq]);
+#pragma unroll
+        for (int ia = 0; ia < R1; ++ia) x[ia] = v[ia];
+    }
+    __syncthreads();
+    for (int task = tid; task < P::ROWS * R1; task += P::THREADS) {
+        const int row = task / R1, ia = task % R1;
+        float2* x = buf + row * P::PITCH;
+        float2 v[R2];
+#pragma unroll
+        for (int qq = 0; qq < R2; ++qq) v[qq] = x[P::pad(ia + R1 * qq)];
+        dft_reg<R2, 1, float>(v);
+#pragma unroll
+        for (int q = 0; q < R2; ++q) x[P::pad(ia + R1 * q)] = v[q];
+    }
+    __syncthreads();
+}
+
+// Copies the table block to shared memory at byte offset `off` (the caller
+// makes it visible with a barrier before the first use).
+template <int N>
+__device__ __forceinline__ float2* load_tables(const BandArgs& a, unsigned char* smem, size_t off) {
+    using P = Cfg<N>;
+    float2* tab = reinterpret_cast<float2*>(smem + off);
+    for (int t = threadIdx.x; t < P::TAB; t += P::THREADS) tab[t] = a.lit_bs[t];
+    return tab;
+}
+
+// Launch 1: item = (plane p0 + i / NRB, rows j1 in [ROWS rb, ROWS rb + ROWS)).
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::THREADS)
+lit_rows(BandArgs a, const float2* __restrict__ grid, float2* __restrict__ ws, int p0) {
+    using P = Cfg<N>;
+    constexpr int M = P::M, L = P::L, NRB = N / P::ROWS;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2* buf = reinterpret_cast<float2*>(smem);                        // [ROWS][PITCH]
+    float2* raw = buf + P::ROWS * P::PITCH;                               // [ROWS][N]
+    const float2* tab = load_tables<N>(a, smem, (size_t)P::ROWS * P::PITCH * 8 + (size_t)P::ROWS * N * 8);
+    const float2 *cin = tab, *cout = tab + 2 * N, *filt = tab + 3 * N, *om = filt + L;
+    const int plane = p0 + blockIdx.x / NRB, rb = blockIdx.x % NRB;
+    const int fb = plane / N, k = plane % N;
+    const float2* g = grid + a.grid_off[a.fidx[fb]] + (size_t)k * N;     // plane k: g[j1 N^2 + j2]
+    const size_t rs = (size_t)N * N;
+    for (int e = threadIdx.x; e < P::ROWS * N; e += P::THREADS) {
+        const int rr = e / N, t = e % N, j1 = rb * P::ROWS + rr;
+        raw[e] = (j1 < M) ? g[(size_t)j1 * rs + t] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    float2* T = ws + a.ws_aux_off + (size_t)(plane - p0) * 2 * N * N;
+#pragma unroll 1
+    for (int s = 0; s < 2; ++s) {
+        const float sg = s ? -1.f : 1.f;
+        for (int e = threadIdx.x; e < P::ROWS * L; e += P::THREADS) {
+            const int rr = e / L, t = e % L, j1 = rb * P::ROWS + rr;
+            float2 v = make_float2(0.f, 0.f);
+            if (j1 < M && t < M) {
+                v = raw[rr * N + t];
+                if (t == 0) {                                  // repeated gamma node folded
+                    const float2 u = raw[rr * N + M];
+                    v.x += sg * u.x;
+                    v.y += sg * u.y;
+                }
+                if (j1 == 0) {                                 // repeated alpha node folded
+                    const float2 u = g[(size_t)M * rs + t];
+                    v.x += sg * u.x;
+                    v.y += sg * u.y;
+                    if (t == 0) {                              // corner: both, sign squared
+                        const float2 c = g[(size_t)M * rs + M];
+                        v.x += c.x;
+                        v.y += c.y;
+                    }
+                }
+                v = cmul(v, cin[s * N + t]);
+            }
+            buf[rr * P::PITCH + P::pad(t)] = v;
+        }
+        __syncthreads();
+        conv_rows<N>(buf, filt, om);
+        for (int e = threadIdx.x; e < P::ROWS * N; e += P::THREADS) {
+            const int rr = e / N, c = e % N, j1 = rb * P::ROWS + rr;
+            if (j1 >= M) continue;
+            const int q = (c - N / 2 + L) % L;
+            T[(size_t)s * N * N + (size_t)j1 * N + c] = cmul(buf[rr * P::PITCH + P::pad(q)], cout[c]);
+        }
+        __syncthreads();
+    }
+}
+
+// Launch 2: item = (plane p0 + i / (2 NCB), sector, columns c in [ROWS cb, ROWS cb + ROWS)).
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::THREADS)
+lit_cols(BandArgs a, float2* __restrict__ ws, int p0) {
+    using P = Cfg<N>;
+    constexpr int M = P::M, L = P::L, NCB = N / P::ROWS, R = P::ROWS;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2* buf = reinterpret_cast<float2*>(smem);                        // [ROWS][PITCH]
+    const float2* tab = load_tables<N>(a, smem, (size_t)P::ROWS * P::PITCH * 8);   // no raw rows here
+    __syncthreads();
+    const float2 *cin = tab, *cout = tab + 2 * N, *filt = tab + 3 * N, *om = filt + L;
+    const int plane = p0 + blockIdx.x / (2 * NCB), s = (blockIdx.x / NCB) & 1, cb = blockIdx.x % NCB;
+    const int fb = plane / N, k = plane % N;
+    const float2* T = ws + a.ws_aux_off + ((size_t)(plane - p0) * 2 + s) * N * N;
+    for (int e = threadIdx.x; e < R * L; e += P::THREADS) {
+        const int cc = e % R, j1 = e / R;                        // R consecutive columns of row j1
+        float2 v = make_float2(0.f, 0.f);
+        if (j1 < M) v = cmul(T[(size_t)j1 * N + cb * R + cc], cin[s * N + j1]);
+        buf[cc * P::PITCH + P::pad(j1)] = v;
+    }
+    __syncthreads();
+    conv_rows<N>(buf, filt, om);
+    const float scale = a.w32[k] / (2.f * (float)M * (float)M);
+    const size_t plane_off = a.ws_off[a.fidx[fb]];
+    for (int e = threadIdx.x; e < R * N; e += P::THREADS) {
+        const int cc = e / N, ni = e % N, mi = cb * R + cc;
+        const int q = (ni - N / 2 + L) % L;
+        float sc = ((ni + mi) & 1) ? -scale : scale;
+        if (s) sc = -sc;
+        float2 v = cmul(buf[cc * P::PITCH + P::pad(q)], cout[ni]);
+        v = (s == 0 && (ni == 0 || mi == 0)) ? make_float2(0.f, 0.f) : make_float2(v.x * sc, v.y * sc);
+        const size_t off = a.ws_tile_major ? (size_t)s * N * N * N + (size_t)mi * N * N + (size_t)(ni >> 2) * 4 * N +
+                                                 (size_t)4 * k + (ni & 3)
+                                           : ((size_t)k * 2 + s) * N * N + (size_t)mi * N + ni;
+        ws[plane_off + off] = v;
+    }
+}
+
+// planes per chunk: the chunk's intermediate (2 N^2 complex per plane) stays
+// near 64 MB, well inside the L2
+inline int chunk_planes(int N) {
+    const size_t per = (size_t)2 * N * N * 8;
+    const size_t p = ((size_t)64 << 20) / per;
+    return (int)(p < 1 ? 1 : (p > 4096 ? 4096 : p));
+}
+
+template <int N>
+static cudaError_t launch_n(const BandArgs& a, const void* grid, void* ws, cudaStream_t st) {
+    using P = Cfg<N>;
+    // launch 1: rows + raw rows + tables; launch 2: rows + tables
+    const size_t smem1 = P::smem_bytes(), smem2 = P::smem_bytes() - (size_t)P::ROWS * N * 8;
+    cudaError_t e = cudaFuncSetAttribute(lit_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lit_cols<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+    if (e != cudaSuccess) return e;
+    const int nplanes = a.nfunc * N, chunk = a.aux_ring;
+    for (int p0 = 0; p0 < nplanes; p0 += chunk) {
+        const int np = nplanes - p0 < chunk ? nplanes - p0 : chunk;
+        lit_rows<N><<<np * (N / P::ROWS), P::THREADS, smem1, st>>>(a, (const float2*)grid, (float2*)ws, p0);
+        lit_cols<N><<<np * 2 * (N / P::ROWS), P::THREADS, smem2, st>>>(a, (float2*)ws, p0);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace litbs
+
+bool fft_literal_bluestein(int N) { return N >= 64 && N <= 512; }
+
+// Host-side Bluestein tables for bandwidth N (FP64, rounded once): see litbs::Cfg.
+void fft_literal_bluestein_tables(int N, std::vector<float2>& out) {
+    const int M = N - 1, L = 2 * N;
+    int R1 = 0;
+    switch (L) {
+        case 128: R1 = Radix<128>::R1; break;
+        case 256: R1 = Radix<256>::R1; break;
+        case 512: R1 = Radix<512>::R1; break;
+        default: R1 = Radix<1024>::R1; break;
+    }
+    const int R2 = L / R1;
+    const double pi = 3.14159265358979323846;
+    auto cis = [&](long num, long den) {             // e^{i pi num/den}, num reduced mod 2 den
+        long r = num % (2 * den);
+        if (r < 0) r += 2 * den;
+        const double ang = pi * (double)r / (double)den;
+        return make_float2((float)cos(ang), (float)sin(ang));
+    };
+    out.assign(3 * N + 2 * L, make_float2(0.f, 0.f));
+    for (int t = 0; t < N; ++t) {
+        out[t] = cis((long)t * t, M);
+        out[N + t] = cis((long)t * t + t, M);
+        const long q = t - N / 2;
+        out[2 * N + t] = cis(q * q, M);
+    }
+    // chirp e^{-i pi u^2/M} on u in [-N/2 - M + 1, N/2 - 1], placed at u mod L
+    std::vector<double> br(L, 0.0), bi(L, 0.0);
+    for (long u = -(long)(N / 2) - M + 1; u <= N / 2 - 1; ++u) {
+        long r = (u * u) % (2L * M);
+        const double ang = -pi * (double)r / (double)M;
+        const int idx = (int)((u % L + L) % L);
+        br[idx] = cos(ang);
+        bi[idx] = sin(ang);
+    }
+    for (int qa = 0; qa < R1; ++qa)
+        for (int qq = 0; qq < R2; ++qq) {
+            const int f = qq + R2 * qa;                  // frequency held at position qa + R1 qq
+            double sr = 0.0, si = 0.0;
+            for (int n = 0; n < L; ++n) {                // forward transform, e^{-2 pi i f n/L}
+                const long r = ((long)f * n) % L;
+                const double ang = -2.0 * pi * (double)r / (double)L;
+                const double c = cos(ang), sn = sin(ang);
+                sr += br[n] * c - bi[n] * sn;
+                si += br[n] * sn + bi[n] * c;
+            }
+            out[3 * N + qa + R1 * qq] = make_float2((float)(sr / L), (float)(si / L));
+        }
+    for (int t = 0; t < L; ++t) {
+        const double ang = 2.0 * pi * (double)t / (double)L;
+        out[3 * N + L + t] = make_float2((float)cos(ang), (float)sin(ang));
+    }
+}
+
 cudaError_t fft_forward_literal_aux(int N, int device, int* ctas, size_t* elems) {
+    if (fft_literal_bluestein(N)) {
+        // chunk of planes whose intermediate T_s (2 N^2 complex per plane) stays in L2
+        *ctas = litbs::chunk_planes(N);
+        *elems = (((size_t)*ctas * 2 * N * N + 31) / 32) * 32;
+        return cudaSuccess;
+    }
     int sms = 0, per = 0;
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) return e;
@@ -226,6 +513,16 @@ cudaError_t fft_forward_literal_aux(int N, int device, int* ctas, size_t* elems)
 
 cudaError_t launch_fft_forward_literal(const BandArgs& a, const void* grid, void* ws, cudaStream_t st) {
     if (a.nfunc <= 0) return cudaSuccess;
+    if (fft_literal_bluestein(a.N)) {
+        if (a.aux_ring < 1 || !a.lit_bs) return cudaErrorInvalidValue;
+        switch (a.N) {
+            case 64: return litbs::launch_n<64>(a, grid, ws, st);
+            case 128: return litbs::launch_n<128>(a, grid, ws, st);
+            case 256: return litbs::launch_n<256>(a, grid, ws, st);
+            case 512: return litbs::launch_n<512>(a, grid, ws, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     if (a.aux_ring < 1 || !a.lit_w || !a.lit_twist) return cudaErrorInvalidValue;
     const long planes = (long)a.nfunc * a.N * 2;
     const int g = planes < a.aux_ring ? (int)planes : a.aux_ring;     // at most one slab per CTA

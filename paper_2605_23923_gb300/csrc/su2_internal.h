@@ -5,6 +5,8 @@
 
 #include <cuda.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 struct su2_plan_s;
@@ -22,6 +24,9 @@ cudaError_t launch_fft_forward_two_phase(const BandArgs& a, const void* grid, vo
 // Complex64 forward DFT on the printed grid (endpoint folded, (N-1)-point DFTs as
 // dense products): CTAs and per-CTA scratch (complex elements), and launch.
 cudaError_t fft_forward_literal_aux(int N, int device, int* ctas, size_t* elems);
+// N >= 64 on the printed grid: Bluestein (chirp-z) DFTs; their host-made tables.
+bool fft_literal_bluestein(int N);
+void fft_literal_bluestein_tables(int N, std::vector<float2>& out);
 cudaError_t launch_fft_forward_literal(const BandArgs& a, const void* grid, void* ws, cudaStream_t st);
 // Two-phase complex64 inverse DFT (N = 128, 256, 512) over the tile-major
 // planes, using the forward's scratch ring.
