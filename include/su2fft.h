@@ -209,6 +209,44 @@ su2_status su2_forward_stage2(su2_plan_t plan, const void* ws, void* coeffs, voi
 su2_status su2_forward_stage2_depth(su2_plan_t plan, int depth, const void* ws, void* coeffs,
                                     void* cuda_stream);
 
+/* Sharded forward transform (a service of this library; the paper's Sec. 6
+ * Propositions make stage 1 independent per beta node and stage 2 independent
+ * per (m, n) pair, so a transform can be split over R GPUs with one exchange of
+ * the stage-1 planes between the two stages).  Rank r computes stage 1 for its
+ * beta nodes k in [k_base, k_base + nk), sends each rank the rows (s, m) that
+ * rank owns, and computes stage 2 for its own rows from what it received; the
+ * coefficients of all ranks together are su2_forward's (bit for bit: every
+ * plane value and every contraction is computed exactly as there).
+ *
+ * Both calls need a plan with one bandwidth N in {64, 128, 256}, complex64,
+ * algorithm SU2_ALGO_TC_BF16X3, on the periodic grid (else SU2_ERR_UNSUPPORTED).
+ * Row index: row = s N + mi, s the sector (0: integer l, 1: half-integer l) and
+ * mi = m + N/2 (s = 0) or m - 1/2 + N/2 (s = 1), 0 <= row < 2N.
+ *
+ * su2_forward_stage1_slab: stage 1 for beta nodes [k_base, k_base + nk) of every
+ * function of the plan.
+ *   grid_slab: device, [nfunc][N (alpha)][nk (beta)][N (gamma)] complex64, the
+ *              grids restricted to those nodes;
+ *   xplanes:   device, output, the exchange layout [2N (row)][nfunc][N/4][nk][4]:
+ *              element (row, f, n/4, k - k_base, n % 4) is F2_s[k][m][n] of
+ *              function f (same values as su2_plane_offset describes), so the rows
+ *              owned by one rank are one contiguous range;
+ *   ws:        the plan's workspace (its stage-1 scratch is used).
+ *   0 <= k_base, 1 <= nk, k_base + nk <= N, else SU2_ERR_INVALID_ARG.
+ *
+ * su2_forward_stage2_rows: stage 2 for rows [row0, row0 + nrows).
+ *   xrecv:  device, [N/nk (source)][nrows][nfunc][N/4][nk][4] complex64: block q
+ *           is the part of source q's xplanes (beta nodes [q nk, q nk + nk)) for
+ *           these rows;
+ *   coeffs: device, su2_coeff_elems elements; exactly the coefficients f^(l)_{mn}
+ *           of the rows' (s, m) are written (the rest is left as it is).
+ *   16 <= nk, nk % 16 == 0, N % nk == 0, 0 <= row0, 1 <= nrows,
+ *   row0 + nrows <= 2N, else SU2_ERR_INVALID_ARG.  No workspace. */
+su2_status su2_forward_stage1_slab(su2_plan_t plan, int k_base, int nk, const void* grid_slab, void* xplanes,
+                                   void* ws, void* cuda_stream);
+su2_status su2_forward_stage2_rows(su2_plan_t plan, int row0, int nrows, int nk, const void* xrecv, void* coeffs,
+                                   void* cuda_stream);
+
 /* Synthesis: coeffs -> grid (Sec. 3 expansion with the (2l+1) factor). */
 su2_status su2_inverse(su2_plan_t plan, const void* coeffs, void* grid, void* ws,
                        void* cuda_stream);

@@ -176,6 +176,36 @@ class Plan:
                                                       _stream_ptr(stream)))
         return out
 
+    def forward_stage1_slab(self, k_base: int, nk: int, grid_slab: torch.Tensor, out: torch.Tensor | None = None,
+                            ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Stage 1 for beta nodes [k_base, k_base + nk) (su2_forward_stage1_slab): grid_slab
+        [nfunc][N][nk][N] -> exchange layout [2N][nfunc][N/4][nk][4] (flat)."""
+        N = self.Ns[0]
+        elems = self.batch * N * nk * N
+        self._check_tensor(grid_slab, elems, "grid_slab")
+        if out is None:
+            out = torch.empty(2 * elems, dtype=self.torch_dtype, device=grid_slab.device)
+        self._check_tensor(out, 2 * elems, "xplanes")
+        ws = self.workspace() if ws is None else ws
+        _abi.check("su2_forward_stage1_slab",
+                   self._lib.su2_forward_stage1_slab(self._h, int(k_base), int(nk), grid_slab.data_ptr(),
+                                                     out.data_ptr(), ws.data_ptr(), _stream_ptr(stream)))
+        return out
+
+    def forward_stage2_rows(self, row0: int, nrows: int, nk: int, xrecv: torch.Tensor,
+                            out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Stage 2 for rows [row0, row0 + nrows) (su2_forward_stage2_rows) from the received
+        exchange layout [N/nk][nrows][nfunc][N/4][nk][4]; writes only those rows' coefficients."""
+        N = self.Ns[0]
+        self._check_tensor(xrecv, nrows * self.batch * N * N, "xrecv")
+        if out is None:
+            out = torch.zeros(self.coeff_elems, dtype=self.torch_dtype, device=xrecv.device)
+        self._check_tensor(out, self.coeff_elems, "coeffs")
+        _abi.check("su2_forward_stage2_rows",
+                   self._lib.su2_forward_stage2_rows(self._h, int(row0), int(nrows), int(nk), xrecv.data_ptr(),
+                                                     out.data_ptr(), _stream_ptr(stream)))
+        return out
+
     def inverse(self, coeffs: torch.Tensor, out: torch.Tensor | None = None, ws: torch.Tensor | None = None,
                 stream=None) -> torch.Tensor:
         self._check_tensor(coeffs, self.coeff_elems, "coeffs")

@@ -64,6 +64,9 @@ SIGNATURES = [
     ("su2_selftest_bounded_wait", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     ("su2_forward_stage2_depth", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 3),
     ("su2_forward_noalloc", ctypes.c_int, [ctypes.c_void_p] * 4),
+    ("su2_forward_stage1_slab", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int] + [ctypes.c_void_p] * 4),
+    ("su2_forward_stage2_rows", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+     + [ctypes.c_void_p] * 3),
     ("su2_inverse", ctypes.c_int, [ctypes.c_void_p] * 5),
     ("su2_backward", ctypes.c_int, [ctypes.c_void_p] * 5),
     ("su2_sync_status", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),

@@ -312,6 +312,14 @@ su2::BandArgs band_args(const su2_plan_s* P, const Band& b) {
     a.lit_twist = b.d_lit_twist;
     a.lit_bs = b.d_lit_bs;
     a.s2_tiles = b.d_s2_tiles;
+    a.nk = b.N;
+    a.k_base = 0;
+    a.xout = nullptr;
+    a.tc_t0 = 0;
+    a.tc_ntiles = 0;
+    a.xrecv = nullptr;
+    a.x_row0 = 0;
+    a.x_nrows = 0;
     for (int c = 0; c < 3; ++c) a.s2_ntiles[c] = b.s2_ntiles[c];
     const size_t n3 = (b.full_group ? 2 : 1) * (size_t)b.N * b.N * b.N;   // elements of one grid
     for (size_t i = 0; i < b.fids.size(); ++i)
@@ -830,6 +838,55 @@ su2_status su2_forward_stage2(su2_plan_t plan, const void* ws, void* coeffs, voi
         if (e != cudaSuccess) return from_cuda(e);
     }
     return SU2_OK;
+}
+
+// Sharded transform: the plan must hold one bandwidth group on the tensor-core
+// path (complex64, N = 64, 128, 256) on the paper's grid.
+static const Band* sharded_band(su2_plan_t plan) {
+    if (plan->bands.size() != 1 || plan->dtype != SU2_C64 ||
+        (plan->flags & (SU2_FLAG_FULL_GROUP | SU2_FLAG_LITERAL_GRID)))
+        return nullptr;
+    const Band& b = plan->bands.begin()->second;
+    if (!b.tc || b.aux_ring <= 0 || !b.s1_two_phase) return nullptr;
+    return &b;
+}
+
+su2_status su2_forward_stage1_slab(su2_plan_t plan, int k_base, int nk, const void* grid_slab, void* xplanes,
+                                   void* ws, void* stream) {
+    su2_status s = check_exec(plan, grid_slab, xplanes, ws);
+    if (s != SU2_OK) return s;
+    const Band* b = sharded_band(plan);
+    if (!b) return SU2_ERR_UNSUPPORTED;
+    if (nk < 1 || k_base < 0 || k_base + nk > b->N) return SU2_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    if (!g.ok) return SU2_ERR_CUDA;
+    su2::BandArgs a = band_args(plan, *b);
+    a.nk = nk;
+    a.k_base = k_base;
+    a.xout = static_cast<float2*>(xplanes);
+    a.grid_group_off = 0;               // the slab is its own buffer: [fb][j1][k][j2], k < nk
+    a.grid_regular = 1;
+    return from_cuda(su2::launch_fft_forward_two_phase(a, grid_slab, ws, (cudaStream_t)stream));
+}
+
+su2_status su2_forward_stage2_rows(su2_plan_t plan, int row0, int nrows, int nk, const void* xrecv, void* coeffs,
+                                   void* stream) {
+    if (!plan || !xrecv || !coeffs) return SU2_ERR_INVALID_ARG;
+    if (!aligned16(xrecv) || !aligned16(coeffs)) return SU2_ERR_ALIGNMENT;    // no workspace is used
+    const Band* b = sharded_band(plan);
+    if (!b) return SU2_ERR_UNSUPPORTED;
+    const int N = b->N;
+    if (nk < 16 || nk % 16 || N % nk || row0 < 0 || nrows < 1 || row0 + nrows > 2 * N) return SU2_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    if (!g.ok) return SU2_ERR_CUDA;
+    su2::BandArgs a = band_args(plan, *b);
+    a.xrecv = static_cast<const float2*>(xrecv);
+    a.nk = nk;
+    a.x_row0 = row0;
+    a.x_nrows = nrows;
+    a.tc_t0 = row0 * (N / 4);           // the tiles of those rows (4 consecutive n each)
+    a.tc_ntiles = nrows * (N / 4);
+    return from_cuda(su2::launch_contract_forward_tc(a, nullptr, coeffs, (cudaStream_t)stream));
 }
 
 su2_status su2_forward_stage2_depth(su2_plan_t plan, int depth, const void* ws, void* coeffs, void* stream) {

@@ -374,6 +374,16 @@ struct BandArgs {
     const float2* lit_twist;      // [2N] e^{i pi u/(N-1)} (literal grid)
     const float2* lit_bs;         // literal grid, N >= 64: Bluestein tables (chirps, filter, twiddles;
                                   // layout in fft_literal.cu); aux_ring then counts planes per chunk
+    // Sharded transform (a function's beta nodes split over several GPUs for stage 1,
+    // its (s, m) rows for stage 2; defaults describe the whole transform):
+    int nk;                       // beta nodes per function in this stage-1 launch (N: all)
+    int k_base;                   // global index of the first of them
+    float2* xout;                 // stage 1 output in the exchange layout [2N][nfunc][N/4][nk][4]
+                                  // (row s N + mi, then function, then n/4, node, n%4); null: planes
+    int tc_t0, tc_ntiles;         // tensor-core stage 2: tiles [t0, t0 + ntiles) (ntiles 0: all)
+    const float2* xrecv;          // tensor-core stage 2 input in the received exchange layout
+                                  // [N/nk][x_nrows][nfunc][N/4][nk][4] (null: the planes)
+    int x_row0, x_nrows;          // the rows s N + mi that xrecv holds
     const int* s2_tiles;          // FP32 contraction tiles by rows of l: L <= 32, then 32 < L <= 64,
                                   // then L > 64, concatenated (tile numbers as Tile<4>::decode takes)
     int s2_ntiles[3];             // tiles in each of those classes

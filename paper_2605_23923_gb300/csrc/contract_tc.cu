@@ -212,7 +212,8 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
     const uint32_t taddr = *tslot;
 
 
-    const int ntiles = 2 * N * (N / NP);
+    // tiles [tc_t0, tc_t0 + ntiles) of the global numbering (all of them by default)
+    const int ntiles = a.tc_ntiles ? a.tc_ntiles : 2 * N * (N / NP);
     const int nbb = (a.nfunc + BM - 1) / BM;
     const int nitems = ntiles * nbb;
 
@@ -224,7 +225,7 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
             uint32_t g = 0;
             for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
                 Tile<NP> tl;
-                tl.decode(N, item / nbb);
+                tl.decode(N, a.tc_t0 + item / nbb);
                 if (!tl.any) continue;
                 const int bb = item % nbb;
                 for (int c = 0; c < NCH; ++c, ++g) {
@@ -232,8 +233,14 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
                     const uint32_t u = g / NSA;
                     if (u > 0) mbar_wait_bounded(&bar_opa[st], (u - 1) & 1, a.err);   // its A operands read
                     mbar_arrive_expect_tx(&bar_full[st], (uint32_t)STAGE_BYTES);
-                    tma_load_5d(smem + OFF_STG + st * SA, &tmap, c * KC * NP, tl.nb, tl.mi, tl.s, bb * BM,
-                                &bar_full[st], pol);
+                    if (a.xrecv) {        // [source][row][fb][n/4][node][n%4], nk nodes per source
+                        const int kg = c * KC;
+                        tma_load_5d(smem + OFF_STG + st * SA, &tmap, (kg % a.nk) * NP, tl.nb, bb * BM,
+                                    tl.s * N + tl.mi - a.x_row0, kg / a.nk, &bar_full[st], pol);
+                    } else {
+                        tma_load_5d(smem + OFF_STG + st * SA, &tmap, c * KC * NP, tl.nb, tl.mi, tl.s, bb * BM,
+                                    &bar_full[st], pol);
+                    }
                 }
             }
         }
@@ -244,7 +251,7 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
             int nexth = 0;
             for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
                 Tile<NP> tl;
-                tl.decode(N, item / nbb);
+                tl.decode(N, a.tc_t0 + item / nbb);
                 if (!tl.any) continue;
                 const int nmma = (tl.L + 15) & ~15;
                 const uint32_t idesc = instr_desc(nmma);
@@ -299,7 +306,7 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
         uint32_t g = 0;
         for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
             Tile<NP> tl;
-            tl.decode(N, item / nbb);
+            tl.decode(N, a.tc_t0 + item / nbb);
             if (!tl.any) continue;
             for (int c = 0; c < NCH; ++c, ++g) {
                 const int st = g % NSA;
@@ -359,7 +366,7 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
         uint32_t g = 0;
         for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
             Tile<NP> tl;
-            tl.decode(N, item / nbb);
+            tl.decode(N, a.tc_t0 + item / nbb);
             if (!tl.any) continue;
             const int Lt = tl.L, nmma = (Lt + 15) & ~15;
             named_sync(1 + grp, 64);                       // previous tile's tables no longer read
@@ -450,7 +457,7 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
         int nexth = 0;
         for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
             Tile<NP> tl;
-            tl.decode(N, item / nbb);
+            tl.decode(N, a.tc_t0 + item / nbb);
             if (!tl.any) continue;
             const int bb = item % nbb;
             const int Lt = tl.L, nmma = (Lt + 15) & ~15;
@@ -578,22 +585,32 @@ static EncodeTiledFn encode_fn() {
 template <int N>
 static cudaError_t launch_n(const BandArgs& a, const void* ws, void* coeffs, cudaStream_t st) {
     CUtensorMap map;
-    // tile-major planes of a function: [s][mi][ni/4][k][ni%4]; one chunk of a tile
-    // (16 nodes x 4 consecutive n) is 512 contiguous bytes per function
-    if (!a.ws_tile_major) return cudaErrorInvalidValue;
-    const cuuint64_t dims[5] = {(cuuint64_t)N * NP, (cuuint64_t)N / NP, (cuuint64_t)N, 2, (cuuint64_t)a.nfunc};
-    const cuuint64_t strides[4] = {(cuuint64_t)N * NP * 8, (cuuint64_t)N * N * 8, (cuuint64_t)N * N * N * 8,
-                                   (cuuint64_t)2 * N * N * N * 8};
-    const cuuint32_t box[5] = {KC * NP, 1, 1, 1, BM};
-    const void* base = (const char*)ws + a.ws_group_off * sizeof(float2);
-    if (!encode_tensor_map_8b(&map, 5, base, dims, strides, box)) return cudaErrorNotSupported;
+    if (a.xrecv) {
+        // received exchange layout [N/nk sources][x_nrows rows][nfunc][N/4][nk][4]: a chunk
+        // (16 nodes x 4 consecutive n) of one function is 512 contiguous bytes (nk % 16 == 0)
+        const cuuint64_t nk = (cuuint64_t)a.nk, n = (cuuint64_t)N, nf = (cuuint64_t)a.nfunc;
+        const cuuint64_t dims[5] = {nk * NP, n / NP, nf, (cuuint64_t)a.x_nrows, n / nk};
+        const cuuint64_t strides[4] = {nk * NP * 8, n * nk * 8, nf * n * nk * 8, (cuuint64_t)a.x_nrows * nf * n * nk * 8};
+        const cuuint32_t box[5] = {KC * NP, 1, BM, 1, 1};
+        if (!encode_tensor_map_8b(&map, 5, a.xrecv, dims, strides, box)) return cudaErrorNotSupported;
+    } else {
+        // tile-major planes of a function: [s][mi][ni/4][k][ni%4]; one chunk of a tile
+        // (16 nodes x 4 consecutive n) is 512 contiguous bytes per function
+        if (!a.ws_tile_major) return cudaErrorInvalidValue;
+        const cuuint64_t dims[5] = {(cuuint64_t)N * NP, (cuuint64_t)N / NP, (cuuint64_t)N, 2, (cuuint64_t)a.nfunc};
+        const cuuint64_t strides[4] = {(cuuint64_t)N * NP * 8, (cuuint64_t)N * N * 8, (cuuint64_t)N * N * N * 8,
+                                       (cuuint64_t)2 * N * N * N * 8};
+        const cuuint32_t box[5] = {KC * NP, 1, 1, 1, BM};
+        const void* base = (const char*)ws + a.ws_group_off * sizeof(float2);
+        if (!encode_tensor_map_8b(&map, 5, base, dims, strides, box)) return cudaErrorNotSupported;
+    }
     auto kern = contract_tc_kernel<N>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int nitems = 2 * N * (N / NP) * ((a.nfunc + BM - 1) / BM);
+    const int nitems = (a.tc_ntiles ? a.tc_ntiles : 2 * N * (N / NP)) * ((a.nfunc + BM - 1) / BM);
     const int grid = sms < nitems ? sms : nitems;
     kern<<<grid, THREADS, SMEM_BYTES, st>>>(a, map, (float2*)coeffs);
     return cudaGetLastError();

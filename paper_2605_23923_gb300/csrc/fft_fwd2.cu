@@ -87,6 +87,11 @@ __device__ __forceinline__ void tma_load_3d_hint(void* dst, const CUtensorMap* m
         ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar)), "l"(policy)
         : "memory");
 }
+// Prefetch of a box into L2 (no shared memory, no completion to wait for).
+__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap* map, int c0, int c1, int c2) {
+    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];"
+                 ::"l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2) : "memory");
+}
 // Tensor store of a box from this CTA's shared memory (bulk async-group) with an
 // L2 eviction policy.  The planes take evict-first: with the default policy a
 // line of the tile-major planes (four beta nodes, written by four B items) was
@@ -147,7 +152,10 @@ __device__ __forceinline__ Item decode(int i, int nplanes, int D) {
     return it;
 }
 
-template <int N, bool FULL>
+// SLAB: a launch over a slab of a.nk beta nodes (starting at a.k_base) writing
+// the exchange layout; otherwise every node of every function (nk = N, a
+// compile-time constant) writing the planes.
+template <int N, bool FULL, bool SLAB = false>
 __global__ void __launch_bounds__(Cfg<N, FULL>::THREADS, Cfg<N, FULL>::BLOCKS_PER_SM)
 fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const __grid_constant__ CUtensorMap omap,
                   const float2* __restrict__ grid, float2* __restrict__ ws, int D, int RING, int discard_ok, int ostore) {
@@ -169,7 +177,8 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const __
     int* sig_rec = slot_item + NS;                             // [NR] counter to increment (-1: end)
 
     const int tid = threadIdx.x;
-    const int nplanes = a.nfunc * N;
+    const int NK = SLAB ? a.nk : N;                            // planes per function in this launch
+    const int nplanes = a.nfunc * NK;
     const int nitems = (nplanes + D) * P::IB;
     float2* ring = ws + a.ws_aux_off;                          // [RING][2][N][N]
     unsigned* doneA = reinterpret_cast<unsigned*>(ring + (size_t)RING * 2 * N * N);
@@ -227,11 +236,13 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const __
         auto pend = [&](int j) -> int& { return j ? pend1 : pend0; };
         auto store_block = [&](int item, const float2* src) {      // lane 0
             const Item ob = decode<N>(item, nplanes, D);
-            const int fb = ob.plane / N, k = ob.plane % N;
+            const int fb = ob.plane / NK, k = ob.plane % NK;
             const int ni0 = (ob.pb * W + N / 2) & (N - 1);
 #pragma unroll
             for (int h = 0; h < N / P::BOXR; ++h) {
-                if (a.ws_tile_major)       // [fb*2 + s][mi][ni/4][k][ni%4]
+                if (SLAB)                  // exchange layout [s N + mi][fb][ni/4][k][ni%4]
+                    tma_store_5d(&omap, src + h * P::BOXR * W, 0, k, ni0 / 4, fb, ob.s * N + h * P::BOXR, pol);
+                else if (a.ws_tile_major)  // [fb*2 + s][mi][ni/4][k][ni%4]
                     tma_store_5d(&omap, src + h * P::BOXR * W, 0, k, ni0 / 4, h * P::BOXR, fb * 2 + ob.s, pol);
                 else                       // [fb][k][s][mi][ni]
                     tma_store_5d(&omap, src + h * P::BOXR * W, ni0, h * P::BOXR, ob.s, k, fb, pol);
@@ -280,7 +291,7 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const __
             const unsigned use = (unsigned)(it.plane / RING);
             float2* dst = S + b * P::SLOTP;
             if (it.isA) {
-                const int fb = it.plane / N, k = it.plane % N;
+                const int fb = it.plane / NK, k = it.plane % NK;
                 if (lane == 0 && use > 0) wait_counter_bounded(&doneB[r], use * P::NB, a.err);
                 constexpr int NSL = FULL ? 2 : 1;                 // slabs per A item
                 constexpr int GN = FULL ? 2 * N : N;              // psi nodes of a grid row
@@ -293,6 +304,17 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const __
                             for (int h = 0; h < N / P::BOXR; ++h)
                                 tma_load_3d_hint(dst + sl * SLOT + h * P::BOXR * W, &gmap, it.jb * W + sl * N, k,
                                                  fb * N + h * P::BOXR, &full[b], pol);
+                        // the same column stripe of the plane PF planes ahead into L2: its A
+                        // item, handed out about PF blocks later, then loads from L2
+                        constexpr int PF = 8;
+                        const int tp = it.plane + PF;
+                        if (tp < nplanes) {
+#pragma unroll
+                            for (int sl = 0; sl < NSL; ++sl)
+#pragma unroll
+                                for (int h = 0; h < N / P::BOXR; ++h)
+                                    tma_prefetch_3d(&gmap, it.jb * W + sl * N, tp % NK, (tp / NK) * N + h * P::BOXR);
+                        }
                     }
                 } else {
                     const float2* src = grid + a.grid_off[a.fidx[fb]] + (size_t)k * GN + it.jb * W;
@@ -339,7 +361,7 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const __
         const Item it = decode<N>(i, nplanes, D);
         float2* X = S + b * P::SLOTP;
         const int r = it.plane % RING;
-        const int fb = it.plane / N, k = it.plane % N;
+        const int fb = it.plane / NK, k = it.plane % NK;       // k: node within this launch
 
         if (it.isA) {
             // Pass a: R2-point DFTs over j1 = ia + R1*b (stride R1), both sectors.
@@ -439,7 +461,7 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const __
                 for (int ia = 0; ia < R1; ++ia) v[ia] = Y[pl * P::PB + ia + R1 * qb];
                 named_sync(2, CT);        // Y read before the next item rewrites it
                 dft_reg<R1, 1, float>(v);
-                const float scale = wk[k] / ((FULL ? 4.f : 2.f) * (float)N * (float)N);
+                const float scale = wk[SLAB ? a.k_base + k : k] / ((FULL ? 4.f : 2.f) * (float)N * (float)N);
                 const size_t plane_off = a.grid_regular ? a.ws_group_off + (size_t)fb * 2 * N * N * N
                                                         : a.ws_off[a.fidx[fb]];
                 const int p = it.pb * W + pl;
@@ -526,7 +548,7 @@ static cudaError_t geometry(int device, int* G, int* D, int* RING) {
     return cudaSuccess;
 }
 
-template <int N, bool FULL>
+template <int N, bool FULL, bool SLAB = false>
 static cudaError_t launch_n(const BandArgs& a, const void* in, void* out, cudaStream_t st) {
     using P = Cfg<N, FULL>;
     int dev = 0, G = 0, D = 0, RING = 0;
@@ -542,13 +564,14 @@ static cudaError_t launch_n(const BandArgs& a, const void* in, void* out, cudaSt
     BandArgs b = a;
     if (b.grid_regular) {
         constexpr int GN = FULL ? 2 * N : N;                      // psi nodes per grid row
-        const cuuint64_t dims[3] = {(cuuint64_t)GN, (cuuint64_t)N, (cuuint64_t)a.nfunc * N};
-        const cuuint64_t strides[2] = {(cuuint64_t)GN * 8, (cuuint64_t)N * GN * 8};
+        // grids [fb][j1][k][j2] with a.nk beta nodes (all N, or a slab of them)
+        const cuuint64_t dims[3] = {(cuuint64_t)GN, (cuuint64_t)a.nk, (cuuint64_t)a.nfunc * N};
+        const cuuint64_t strides[2] = {(cuuint64_t)GN * 8, (cuuint64_t)a.nk * GN * 8};
         const cuuint32_t box[3] = {(cuuint32_t)P::W, 1, (cuuint32_t)P::BOXR};
         const void* base = (const float2*)in + a.grid_group_off;
         if (!encode_tensor_map_8b(&gmap, 3, base, dims, strides, box)) b.grid_regular = 0;
     }
-    const int nitems = (a.nfunc * N + D) * P::IB;
+    const int nitems = (a.nfunc * a.nk + D) * P::IB;
     int grid = G < nitems ? G : nitems;
     // SU2_STAGE1_MAX_CTAS caps the grid (robustness checks: the in-order queue
     // must finish with any number of resident CTAs, down to one)
@@ -562,7 +585,13 @@ static cudaError_t launch_n(const BandArgs& a, const void* in, void* out, cudaSt
     CUtensorMap omap;
     memset(&omap, 0, sizeof(omap));
     int ostore = 0;
-    if (b.grid_regular) {
+    if (b.grid_regular && a.xout) {   // exchange layout [s N + mi][fb][ni/4][k][ni%4], k < nk
+        const cuuint64_t n = (cuuint64_t)N, e = 8, nk = (cuuint64_t)a.nk;
+        const cuuint64_t dims[5] = {4, nk, n / 4, (cuuint64_t)a.nfunc, 2 * n};
+        const cuuint64_t strides[4] = {4 * e, nk * 4 * e, n * nk * e, (cuuint64_t)a.nfunc * n * nk * e};
+        const cuuint32_t box[5] = {4, 1, (cuuint32_t)P::W / 4, 1, (cuuint32_t)P::BOXR};
+        ostore = encode_tensor_map_8b(&omap, 5, a.xout, dims, strides, box) ? 1 : 0;
+    } else if (b.grid_regular) {
         const cuuint64_t n = (cuuint64_t)N, e = 8;
         const void* base = (const float2*)out + a.ws_group_off;
         if (a.ws_tile_major) {         // [fb*2 + s][mi][ni/4][k][ni%4]
@@ -577,8 +606,15 @@ static cudaError_t launch_n(const BandArgs& a, const void* in, void* out, cudaSt
             ostore = encode_tensor_map_8b(&omap, 5, base, dims, strides, box) ? 1 : 0;
         }
     }
-    fft_fwd_two_phase<N, FULL><<<grid, P::THREADS, P::smem_bytes(), st>>>(b, gmap, omap, (const float2*)in,
-                                                                         (float2*)out, D, RING, discard_ok, ostore);
+    // the exchange layout is written by tensor stores only
+    if (a.xout && (!b.grid_regular || !ostore)) return cudaErrorNotSupported;
+    if (SLAB != (a.xout != nullptr)) return cudaErrorInvalidValue;
+    auto kern = fft_fwd_two_phase<N, FULL, SLAB>;
+    if (SLAB && (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::smem_bytes())) !=
+                    cudaSuccess)
+        return e;
+    kern<<<grid, P::THREADS, P::smem_bytes(), st>>>(b, gmap, omap, (const float2*)in, (float2*)out, D, RING,
+                                                    discard_ok, ostore);
     return cudaGetLastError();
 }
 
@@ -615,6 +651,15 @@ cudaError_t fft_forward_aux(int N, int device, bool full_group, int* ring, size_
 
 cudaError_t launch_fft_forward_two_phase(const BandArgs& a, const void* grid, void* ws, cudaStream_t st) {
     if (a.nfunc <= 0) return cudaSuccess;
+    if (a.xout) {                       // beta slab -> exchange layout (sharded transform)
+        if (a.full_group) return cudaErrorInvalidValue;
+        switch (a.N) {
+            case 64: return fwd2::launch_n<64, false, true>(a, grid, ws, st);
+            case 128: return fwd2::launch_n<128, false, true>(a, grid, ws, st);
+            case 256: return fwd2::launch_n<256, false, true>(a, grid, ws, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     if (a.full_group) {
         switch (a.N) {
             case 64: return fwd2::launch_n<64, true>(a, grid, ws, st);
