@@ -106,10 +106,18 @@ typedef struct {
  *   it with one graph launch on the caller's stream.  The plan keeps the 8
  *   most recent graphs.  The first call with new pointers must not itself be
  *   made during a stream capture.
- * SU2_FLAG_AUTOTUNE: su2_plan times the candidate kernels of every complex64
- *   bandwidth group (forward 2-D DFT variant at N = 64, 128; functions per
- *   block of the FP32 contraction) on scratch buffers it allocates and frees,
- *   and keeps the fastest.  Results do not depend on the choice. */
+ * SU2_FLAG_AUTOTUNE: su2_plan times, for every complex64 bandwidth group on
+ *   the periodic grid, stage 1 + stage 2 of each candidate on scratch buffers
+ *   it allocates and frees (min(group size, 64) functions) and keeps the
+ *   fastest: the tensor-core contraction (SU2_ALGO_TC_BF16X3 plans, N = 64..256)
+ *   or the FP32 one, the stage-1 variant (two-phase, or the DSMEM cluster one
+ *   at N = 64, 128), and the FP32 contraction's form (row classes, or 8 or 16
+ *   functions per block).  A group that ends on the FP32 contraction keeps its
+ *   stage-1 planes in the plain layout (su2_plane_offset).  With the
+ *   environment variable SU2_TUNE_CACHE set to a file path, choices are read
+ *   from that JSON file (keyed by device name, SM count, N, group size,
+ *   algorithm, weights, grid) and new ones are added to it.  Results do not
+ *   depend on the choice beyond rounding of the contraction arithmetic. */
 #define SU2_FLAG_CUDA_GRAPH 0x1u
 #define SU2_FLAG_AUTOTUNE 0x2u
 /* SU2_FLAG_FULL_GROUP: grids are sampled on the full group, psi (gamma) over
@@ -119,8 +127,9 @@ typedef struct {
  * 1/(4N^2).  On the paper's domain (Sec. 4, psi over [-pi, pi]) the integer-l
  * and half-integer-l sectors are not orthogonal; on the full group they are,
  * and a band-limited function mixing both sectors is recovered exactly.
- * complex64, N = 64, 128, 256, forward transform only (su2_inverse and
- * su2_backward return SU2_ERR_UNSUPPORTED for such plans). */
+ * complex64, N = 64, 128, 256; su2_inverse and su2_backward (adjoint prefactor
+ * 1/(4N^2)) for plans whose bandwidths are all 128 or 256, else
+ * SU2_ERR_UNSUPPORTED. */
 #define SU2_FLAG_FULL_GROUP 0x4u
 /* SU2_FLAG_LITERAL_GRID: grids are sampled on the grid as Sec. 4 prints it,
  * alpha_j = gamma_j = -pi + 2 pi j/(N-1), j = 0..N-1 (the last node, +pi,
@@ -158,7 +167,8 @@ su2_status su2_workspace_size(su2_plan_t plan, size_t* bytes);
  * with mi = m + N/2, ni = n + N/2 for s = 0 (row and column 0 unused, zero)
  * and mi = m - 1/2 + N/2, ni = n - 1/2 + N/2 for s = 1 (Sec. 6 first-stage
  * Proposition; Sec. 4 grid).  Plans of algorithm SU2_ALGO_TC_BF16X3 store the
- * same values tile-major instead: element (k, s, mi, ni) at that offset +
+ * same values tile-major instead (except groups the autotuner moved to the
+ * FP32 contraction): element (k, s, mi, ni) at that offset +
  * s N^3 + mi N^2 + (ni / 4) 4N + 4k + ni % 4 (four consecutive n of all beta
  * nodes contiguous, the operand tiles of the tensor-core contraction). */
 su2_status su2_plane_offset(su2_plan_t plan, int f, size_t* elems);

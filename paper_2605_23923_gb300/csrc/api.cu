@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -19,6 +21,7 @@
 #include <cmath>
 #include <map>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "../../include/su2fft.h"
@@ -51,6 +54,7 @@ struct Band {
     float2* d_lit_bs = nullptr;
     int s1_two_phase = 0;         // kernel choices (defaults, or the autotuner's)
     int s2_bt = 0;
+    int s2_rc = -1;               // FP32 row classes: -1 by batch size, 0 off, 1 on
     int* d_s2_tiles = nullptr;    // FP32 contraction tiles grouped by rows of l (see BandArgs)
     int s2_ntiles[3] = {0, 0, 0};
 };
@@ -306,6 +310,7 @@ su2::BandArgs band_args(const su2_plan_s* P, const Band& b) {
     a.ws_tile_major = b.tc ? 1 : 0;
     a.s1_two_phase = b.s1_two_phase;
     a.s2_bt = b.s2_bt;
+    a.s2_rc = b.s2_rc;
     a.full_group = b.full_group ? 1 : 0;
     a.literal = b.literal ? 1 : 0;
     a.lit_w = b.d_lit_w;
@@ -487,18 +492,127 @@ cudaError_t time_ms(cudaStream_t st, float* ms, const std::function<cudaError_t(
     return e;
 }
 
+// One group's kernel choice: contraction on tensor cores (tile-major planes) or
+// FP32 (plain planes), stage-1 variant, FP32 contraction form.
+struct TuneChoice {
+    int tc = 0;      // 1: tensor-core contraction
+    int s1 = 1;      // 1: two-phase stage 1, 0: DSMEM cluster stage 1
+    int rc = 1;      // FP32: 1 row classes, 0 one launch with bt functions per block
+    int bt = 16;     // FP32 without row classes: 8 or 16 functions per block
+};
+
+// Autotuner cache (SU2_TUNE_CACHE = path of a JSON file): one object per group
+// key, {"tc": 0|1, "s1": 0|1, "rc": 0|1, "bt": 8|16}.  Read before tuning, merged
+// and rewritten (temporary file + rename) after.
+std::map<std::string, TuneChoice> read_tune_cache(const char* path) {
+    std::map<std::string, TuneChoice> out;
+    FILE* f = path ? fopen(path, "rb") : nullptr;
+    if (!f) return out;
+    std::string text;
+    char buf[4096];
+    size_t n;
+    while ((n = fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, n);
+    fclose(f);
+    size_t pos = 0;
+    auto read_str = [&](std::string& str) -> bool {
+        const size_t a = text.find('"', pos);
+        if (a == std::string::npos) return false;
+        const size_t b = text.find('"', a + 1);
+        if (b == std::string::npos) return false;
+        str = text.substr(a + 1, b - a - 1);
+        pos = b + 1;
+        return true;
+    };
+    for (;;) {
+        std::string key;
+        if (!read_str(key)) break;
+        const size_t open = text.find('{', pos), close = text.find('}', pos);
+        if (open == std::string::npos || close == std::string::npos || open > close) break;
+        TuneChoice c;
+        const std::string body = text.substr(open + 1, close - open - 1);
+        auto field = [&](const char* name, int* v) {
+            const size_t q = body.find(std::string("\"") + name + "\"");
+            if (q == std::string::npos) return;
+            const size_t colon = body.find(':', q);
+            if (colon != std::string::npos) *v = atoi(body.c_str() + colon + 1);
+        };
+        field("tc", &c.tc);
+        field("s1", &c.s1);
+        field("rc", &c.rc);
+        field("bt", &c.bt);
+        if (c.bt != 8) c.bt = 16;
+        out[key] = c;
+        pos = close + 1;
+    }
+    return out;
+}
+
+void write_tune_cache(const char* path, const std::map<std::string, TuneChoice>& m) {
+    if (!path) return;
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* f = fopen(tmp.c_str(), "wb");
+    if (!f) return;
+    fprintf(f, "{\n");
+    size_t i = 0;
+    for (const auto& kv : m) {
+        fprintf(f, "  \"%s\": {\"tc\": %d, \"s1\": %d, \"rc\": %d, \"bt\": %d}%s\n", kv.first.c_str(), kv.second.tc,
+                kv.second.s1, kv.second.rc, kv.second.bt, ++i < m.size() ? "," : "");
+    }
+    fprintf(f, "}\n");
+    fclose(f);
+    rename(tmp.c_str(), path);
+}
+
+std::string tune_key(const su2_plan_s* P, int N, int nfunc) {
+    cudaDeviceProp prop;
+    std::string name = "device";
+    int sms = 0;
+    if (cudaGetDeviceProperties(&prop, P->device) == cudaSuccess) {
+        name = prop.name;
+        sms = prop.multiProcessorCount;
+    }
+    for (char& ch : name)
+        if (ch == '"' || ch == '\\') ch = '_';
+    char k[256];
+    snprintf(k, sizeof(k), "%s|sm%d|N%d|nf%d|algo%d|w%d|g%u|v1", name.c_str(), sms, N, nfunc, (int)P->algo,
+             (int)P->weights, P->flags & (SU2_FLAG_FULL_GROUP | SU2_FLAG_LITERAL_GRID));
+    return k;
+}
+
+void apply_choice(Band& b, const TuneChoice& c) {
+    b.tc = c.tc != 0;
+    b.s1_two_phase = c.s1;
+    b.s2_rc = c.rc;
+    b.s2_bt = c.bt;
+}
+
+// For each complex64 group on the paper's grid: time, on scratch buffers with
+// min(group size, 64) functions, stage 1 + stage 2 for every candidate -- the
+// tensor-core contraction (tensor-core plans, N = 64..256) and the FP32
+// contraction with each stage-1 variant (two-phase; the DSMEM cluster one at
+// N = 64, 128) and each FP32 form (row classes; 8 or 16 functions per block) --
+// and keep the fastest.  Results do not depend on the choice.
 cudaError_t autotune(su2_plan_s* P) {
     if (P->dtype != SU2_C64) return cudaSuccess;
+    const char* cache_path = getenv("SU2_TUNE_CACHE");
+    std::map<std::string, TuneChoice> cache = read_tune_cache(cache_path);
+    bool cache_dirty = false;
     cudaStream_t st;
     cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     if (e != cudaSuccess) return e;
     for (auto& kv : P->bands) {
         Band& b = kv.second;
         const int N = kv.first;
-        const bool try_s1 = b.aux_ring > 0 && !b.tc && !b.full_group && !b.literal && (N == 64 || N == 128);
-        const bool try_s2 = !b.tc;
-        if (!try_s1 && !try_s2) continue;
-        const int nb = std::min((int)b.fids.size(), 32);
+        if (b.full_group || b.literal) continue;
+        const bool can_tc = b.tc;                       // tensor-core plan and a supported N
+        const bool can_s1 = b.aux_ring > 0 && (N == 64 || N == 128);
+        const int nb = std::min((int)b.fids.size(), 64);
+        const std::string key = tune_key(P, N, (int)b.fids.size());
+        auto hit = cache.find(key);
+        if (hit != cache.end() && (hit->second.tc == 0 || can_tc) && (hit->second.s1 == 1 ? b.aux_ring > 0 : true)) {
+            apply_choice(b, hit->second);
+            continue;
+        }
         const size_t n3 = (size_t)N * N * N;
         std::vector<int> fidx(nb);
         std::vector<size_t> goff(nb), coff(nb), woff(nb);
@@ -525,6 +639,12 @@ cudaError_t autotune(su2_plan_s* P) {
         if (e == cudaSuccess) e = cudaMemcpyAsync(dwo, woff.data(), nb * sizeof(size_t), cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(dfi, fidx.data(), nb * sizeof(int), cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        // the FP32 contraction's row-class tile list, also for tensor-core groups
+        if (e == cudaSuccess && !b.d_s2_tiles) {
+            std::vector<int> tiles;
+            fp32_tile_classes(N, tiles, b.s2_ntiles);
+            e = P->upload(&b.d_s2_tiles, tiles.data(), tiles.size());
+        }
         su2::BandArgs t = band_args(P, b);
         t.nfunc = nb;
         t.fidx = dfi;
@@ -535,29 +655,37 @@ cudaError_t autotune(su2_plan_s* P) {
         t.grid_group_off = 0;
         t.grid_regular = 1;
         t.ws_aux_off = (size_t)nb * 2 * n3;
-        if (e == cudaSuccess && try_s1) {
-            float best = 1e30f;
-            int pick = b.s1_two_phase;
-            for (int cand = 0; cand < 2 && e == cudaSuccess; ++cand) {
-                t.s1_two_phase = cand;
-                float ms = 0.f;
-                e = time_ms(st, &ms, [&]() { return su2::launch_fft_forward(t, false, dg, dw, st); });
-                if (e == cudaSuccess && ms < best) { best = ms; pick = cand; }
-            }
-            b.s1_two_phase = pick;
-            t.s1_two_phase = pick;
+        t.s2_tiles = b.d_s2_tiles;
+        for (int c = 0; c < 3; ++c) t.s2_ntiles[c] = b.s2_ntiles[c];
+        std::vector<TuneChoice> cands;
+        if (can_tc) cands.push_back(TuneChoice{1, 1, 1, 16});
+        for (int s1 : {1, 0}) {
+            if (s1 == 1 && b.aux_ring <= 0) continue;
+            if (s1 == 0 && !(can_s1 || b.aux_ring <= 0)) continue;
+            if (nb >= 48) cands.push_back(TuneChoice{0, s1, 1, 16});
+            cands.push_back(TuneChoice{0, s1, 0, 8});
+            cands.push_back(TuneChoice{0, s1, 0, 16});
         }
-        if (e == cudaSuccess && try_s2) {
-            float best = 1e30f;
-            int pick = 0;
-            for (int cand : {8, 16}) {
-                if (e != cudaSuccess) break;
-                t.s2_bt = cand;
-                float ms = 0.f;
-                e = time_ms(st, &ms, [&]() { return su2::launch_contract_forward(t, false, dw, dc, st); });
-                if (e == cudaSuccess && ms < best) { best = ms; pick = cand; }
+        TuneChoice best_c;
+        float best = 1e30f;
+        for (const TuneChoice& c : cands) {
+            if (e != cudaSuccess) break;
+            su2::BandArgs u = t;
+            u.ws_tile_major = c.tc;
+            u.s1_two_phase = c.s1;
+            u.s2_rc = c.rc;
+            u.s2_bt = c.bt;
+            float ms = 0.f;
+            e = time_ms(st, &ms, [&]() {
+                cudaError_t ee = su2::launch_fft_forward(u, false, dg, dw, st);
+                if (ee != cudaSuccess) return ee;
+                return c.tc ? su2::launch_contract_forward_tc(u, dw, dc, st)
+                            : su2::launch_contract_forward(u, false, dw, dc, st);
+            });
+            if (e == cudaSuccess && ms < best) {
+                best = ms;
+                best_c = c;
             }
-            b.s2_bt = pick;
         }
         cudaStreamSynchronize(st);
         if (dg) cudaFree(dg);
@@ -565,8 +693,14 @@ cudaError_t autotune(su2_plan_s* P) {
         if (dc) cudaFree(dc);
         if (dt) cudaFree(dt);
         if (e != cudaSuccess) break;
+        if (!cands.empty()) {
+            apply_choice(b, best_c);
+            cache[key] = best_c;
+            cache_dirty = true;
+        }
     }
     cudaStreamDestroy(st);
+    if (e == cudaSuccess && cache_dirty) write_tune_cache(cache_path, cache);
     return e;
 }
 
@@ -909,7 +1043,10 @@ static su2_status run_transpose(su2_plan_t plan, su2::TransposeMode mode, const 
                                 void* ws, void* stream) {
     su2_status s = check_exec(plan, coeffs, grid, ws);
     if (s != SU2_OK) return s;
-    if (plan->flags & (SU2_FLAG_FULL_GROUP | SU2_FLAG_LITERAL_GRID)) return SU2_ERR_UNSUPPORTED;   // forward only
+    if (plan->flags & SU2_FLAG_LITERAL_GRID) return SU2_ERR_UNSUPPORTED;   // printed grid: forward only
+    if (plan->flags & SU2_FLAG_FULL_GROUP)                                 // full group: N = 128, 256
+        for (const auto& kv : plan->bands)
+            if ((kv.first != 128 && kv.first != 256) || kv.second.aux_ring <= 0) return SU2_ERR_UNSUPPORTED;
     DeviceGuard g(plan->device);
     if (!g.ok) return SU2_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;

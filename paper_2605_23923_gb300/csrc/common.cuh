@@ -367,6 +367,7 @@ struct BandArgs {
                                   // (tensor-core plans), 0: [k][s][mi][ni]
     int s1_two_phase;             // forward 2-D DFT: 1 two-phase kernel (needs aux_ring > 0), 0 cluster
     int s2_bt;                    // FP32 forward contraction: functions per block (8 or 16; 0: by batch)
+    int s2_rc;                    // FP32 forward contraction in row classes: -1 when >= 48 functions, 0 no, 1 yes
     int full_group;               // grids on the full-group grid (psi over [-2 pi, 2 pi), 2N nodes)
     int literal;                  // grids on the printed grid (spacing 2 pi/(N-1), endpoint repeated);
                                   // aux_ring then counts the literal kernel's CTAs (one N^2 slab each)

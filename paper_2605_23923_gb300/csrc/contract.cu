@@ -583,7 +583,9 @@ contract_tr32(BandArgs a, int mode, const float2* __restrict__ coeffs, float2* _
     const SeedPair q0 = spair[2 * h], q1 = spair[2 * h + 1];
     const StepCoef<float>* c0p = coef + (2 * h) * RS;
     const StepCoef<float>* c1p = coef + (2 * h + 1) * RS;
-    const float inv2n2 = 1.f / (2.f * (float)N * (float)N);
+    // adjoint prefactor: the grid cell over the Haar measure, 1/(2N^2) on the paper's
+    // domain, 1/(4N^2) on the full group (psi over 4 pi)
+    const float inv2n2 = 1.f / ((a.full_group ? 4.f : 2.f) * (float)N * (float)N);
     const int ni0 = tl.nb * NB + 2 * h;
 
     for (int pass = 0; pass < P::PASSES; ++pass) {
@@ -739,7 +741,7 @@ static cudaError_t launch_fwd_t(const BandArgs& a, const void* ws, void* coeffs,
 cudaError_t launch_contract_forward(const BandArgs& a, bool fp64, const void* ws, void* coeffs, cudaStream_t st) {
     if (a.nfunc <= 0) return cudaSuccess;
     if (fp64) return launch_fwd_t<double, 4, 8, 32, 64, 4, 2>(a, ws, coeffs, st);
-    if (a.s2_tiles && a.nfunc >= 48) {
+    if (a.s2_tiles && (a.s2_rc > 0 || (a.s2_rc < 0 && a.nfunc >= 48))) {
         // Large batches: one launch per row class, each with a row window that fits
         // its tiles (32, 64, 128 rows of l) and the threads that a window of all 128
         // rows would leave idle on short tiles spent on more functions (64, 32, 16

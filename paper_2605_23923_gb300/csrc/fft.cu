@@ -925,6 +925,8 @@ cudaError_t launch_fft_forward(const BandArgs& a, bool fp64, const void* grid, v
 }
 
 cudaError_t launch_fft_inverse(const BandArgs& a, bool fp64, const void* ws, void* grid, cudaStream_t st) {
+    if (a.full_group)                   // two-phase only (N = 128, 256; the caller checks)
+        return (a.aux_ring > 0 && !fp64) ? launch_fft_inverse_two_phase(a, ws, grid, st) : cudaErrorInvalidValue;
     if (a.aux_ring > 0 && a.ws_tile_major && fft_inverse_two_phase_supported(a.N, fp64))
         return launch_fft_inverse_two_phase(a, ws, grid, st);
     return fp64 ? launch_any<double, false>(a, ws, grid, st) : launch_any<float, false>(a, ws, grid, st);

@@ -15,6 +15,12 @@
 //       over q -> untwist e^{-i pi j2 s/N} -> sector sum -> 16 grid rows of N
 //       contiguous nodes j2.
 //
+// Full-group grid (template FULL, psi over [-2 pi, 2 pi) with 2N nodes,
+// psi_j = gamma_{(j - N/2) mod N} - 2 pi [j < N/2] + 2 pi [j >= 3N/2]): a
+// half-integer m changes sign over 2 pi, so the grid row is f_int + f_half at
+// j in [N/2, 3N/2) and f_int - f_half at the other N nodes, from the same two
+// sector sums.
+//
 // The intermediate ring, its counters and the in-order item queue are the
 // forward two-phase DFT's scratch (the same workspace region; a plan's calls on
 // one workspace are serialised).  Items: block t holds the A items of plane t
@@ -50,7 +56,7 @@ __device__ __forceinline__ void discard_line(const void* p) {
     asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
 }
 
-template <int N>
+template <int N, bool FULL = false>
 __global__ void __launch_bounds__(Cfg<N>::THREADS, Cfg<N>::BLOCKS_PER_SM)
 fft_inv_two_phase(BandArgs a, const float2* __restrict__ ws, float2* __restrict__ grid, int D, int RING,
                   int discard_ok) {
@@ -202,25 +208,37 @@ fft_inv_two_phase(BandArgs a, const float2* __restrict__ ws, float2* __restrict_
                 for (int ia = 0; ia < R1; ++ia) v[ia] = X1[ia * (R2 + 1)];
                 dft_reg<R1, -1, float>(v);
                 const int j1 = jb * W + cb;
-                float2* out = grid + a.grid_off[f] + (size_t)j1 * N * N + (size_t)k * N + qb;
+                if constexpr (FULL) {
+                    float2* out = grid + a.grid_off[f] + (size_t)j1 * N * 2 * N + (size_t)k * 2 * N;
 #pragma unroll
-                for (int qa = 0; qa < R1; ++qa) {
-                    const float2 w = cmul(v[qa], ut[qb + R2 * qa]);
-                    const float2 z = X0[qa * (R2 + 1)];
-                    __stcs(out + R2 * qa, make_float2(w.x + z.x, w.y + z.y));
+                    for (int qa = 0; qa < R1; ++qa) {
+                        const int j2 = qb + R2 * qa;
+                        const float2 w = cmul(v[qa], ut[j2]);
+                        const float2 z = X0[qa * (R2 + 1)];
+                        __stcs(out + j2 + N / 2, make_float2(z.x + w.x, z.y + w.y));
+                        __stcs(out + ((j2 + 3 * N / 2) & (2 * N - 1)), make_float2(z.x - w.x, z.y - w.y));
+                    }
+                } else {
+                    float2* out = grid + a.grid_off[f] + (size_t)j1 * N * N + (size_t)k * N + qb;
+#pragma unroll
+                    for (int qa = 0; qa < R1; ++qa) {
+                        const float2 w = cmul(v[qa], ut[qb + R2 * qa]);
+                        const float2 z = X0[qa * (R2 + 1)];
+                        __stcs(out + R2 * qa, make_float2(w.x + z.x, w.y + z.y));
+                    }
                 }
             }
         }
     }
 }
 
-template <int N>
+template <int N, bool FULL>
 static cudaError_t geometry(int device, int* G, int* D) {
     using P = Cfg<N>;
     int sms = 0, per = 0;
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) return e;
-    auto kern = fft_inv_two_phase<N>;
+    auto kern = fft_inv_two_phase<N, FULL>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::smem_bytes());
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, P::THREADS, P::smem_bytes());
@@ -232,13 +250,13 @@ static cudaError_t geometry(int device, int* G, int* D) {
     return cudaSuccess;
 }
 
-template <int N>
+template <int N, bool FULL = false>
 static cudaError_t launch_n(const BandArgs& a, const void* ws, void* grid, cudaStream_t st) {
     using P = Cfg<N>;
     int dev = 0, G = 0, D = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if ((e = geometry<N>(dev, &G, &D)) != cudaSuccess) return e;
+    if ((e = geometry<N, FULL>(dev, &G, &D)) != cudaSuccess) return e;
     // the forward's ring and counters (same scratch); any lag D < RING keeps the
     // slot-reuse waits pointing at smaller item numbers
     const int RING = a.aux_ring;
@@ -250,8 +268,8 @@ static cudaError_t launch_n(const BandArgs& a, const void* ws, void* grid, cudaS
     const int nitems = (a.nfunc * N + D) * P::IB;
     const int g = G < nitems ? G : nitems;
     const int discard_ok = ((uintptr_t)ring % 128) == 0;
-    fft_inv_two_phase<N><<<g, P::THREADS, P::smem_bytes(), st>>>(a, (const float2*)ws, (float2*)grid, D, RING,
-                                                               discard_ok);
+    fft_inv_two_phase<N, FULL><<<g, P::THREADS, P::smem_bytes(), st>>>(a, (const float2*)ws, (float2*)grid, D,
+                                                                     RING, discard_ok);
     return cudaGetLastError();
 }
 
@@ -261,6 +279,13 @@ bool fft_inverse_two_phase_supported(int N, bool fp64) { return !fp64 && (N == 1
 
 cudaError_t launch_fft_inverse_two_phase(const BandArgs& a, const void* ws, void* grid, cudaStream_t st) {
     if (a.nfunc <= 0) return cudaSuccess;
+    if (a.full_group) {
+        switch (a.N) {
+            case 128: return inv2::launch_n<128, true>(a, ws, grid, st);
+            case 256: return inv2::launch_n<256, true>(a, ws, grid, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (a.N) {
         case 128: return inv2::launch_n<128>(a, ws, grid, st);
         case 256: return inv2::launch_n<256>(a, ws, grid, st);

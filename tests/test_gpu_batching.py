@@ -91,3 +91,33 @@ def test_graph_replay_follows_new_inputs(su2, algo):
     out2 = plan.forward(x2)
     plan.sync_status()
     assert torch.equal(out2, plain.forward(x2))
+
+
+def test_ragged_tensor_core_autotune_and_cache(su2, tmp_path, monkeypatch):
+    """A tensor-core plan over the ragged batch with the autotuner (which may move
+    a group to the FP32 contraction) against the oracle-checked plain plan; the
+    choices go to the SU2_TUNE_CACHE file, and a second plan that reads them
+    gives the same coefficients bit for bit."""
+    import json
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("SU2_TUNE_CACHE", str(cache))
+    rng = np.random.default_rng(31)
+    Ns = I.draw_ragged_bandwidths(96, (16, 32, 64, 128), rng)
+    plan = su2.Plan(Ns=Ns, dtype="c64", algo="tc_bf16x3", graph=True, autotune=True)
+    plain = su2.Plan(Ns=Ns, dtype="c64", algo="fp32")
+    x = torch.randn(plan.grid_elems, dtype=torch.complex64, device="cuda",
+                    generator=torch.Generator(device="cuda").manual_seed(31))
+    out = plan.forward(x)
+    ref = plain.forward(x)
+    plan.sync_status()
+    d = (out - ref).abs().max().item() / ref.abs().max().item()
+    assert d < TOL, d
+    entries = json.loads(cache.read_text())
+    assert len(entries) == 4                          # one per bandwidth group
+    for v in entries.values():
+        assert set(v) == {"tc", "s1", "rc", "bt"}
+    again = su2.Plan(Ns=Ns, dtype="c64", algo="tc_bf16x3", autotune=True)
+    out2 = again.forward(x)
+    again.sync_status()
+    assert torch.equal(out2, out)
+    assert json.loads(cache.read_text()) == entries

@@ -81,7 +81,41 @@ def test_full_group_recovers_mixed_sectors(su2):
     assert _rel(o, c) < TOL
 
 
-def test_full_group_ragged_and_forward_only(su2):
+@pytest.mark.parametrize("algo", ["fp32", "tc_bf16x3"])
+def test_full_group_inverse_and_adjoint_n128(su2, algo):
+    """Synthesis and adjoint on the full-group grid against the oracle, every
+    grid point of two functions (2N = 256 psi nodes)."""
+    N, B = 128, 2
+    rng = np.random.default_rng(74)
+    cs = [I.draw_coeffs(N, rng, "inv1").astype(np.complex64) for _ in range(B)]
+    plan = su2.Plan(N=N, batch=B, dtype="c64", algo=algo, full_group=True)
+    c_dev = torch.from_numpy(np.concatenate(cs)).cuda()
+    syn = plan.inverse(c_dev).cpu().numpy().astype(np.complex128)
+    adj = plan.backward(c_dev).cpu().numpy().astype(np.complex128)
+    plan.sync_status()
+    for b in range(B):
+        o = plan.grid_offsets[b]
+        c64 = cs[b].astype(np.complex128)
+        got_s = syn[o:o + 2 * N ** 3].reshape(N, N, 2 * N)
+        got_a = adj[o:o + 2 * N ** 3].reshape(N, N, 2 * N)
+        assert _rel(got_s, T.inverse_separable(c64, N, full=True)) < TOL, ("synthesis", b)
+        assert _rel(got_a, T.adjoint_separable(c64, N, full=True)) < TOL, ("adjoint", b)
+
+
+@pytest.mark.parametrize("N", [128, 256])
+def test_full_group_round_trip_mixed_sectors(su2, N):
+    """forward(inverse(c)) = c for coefficients in both sectors at once: exact
+    on the full group (Peter-Weyl orthogonality over all of SU(2))."""
+    rng = np.random.default_rng(75 + N)
+    c = I.draw_coeffs(N, rng, "inv1").astype(np.complex64)
+    plan = su2.Plan(N=N, batch=1, dtype="c64", algo="fp32", full_group=True)
+    back = plan.forward(plan.inverse(torch.from_numpy(c).cuda()))
+    plan.sync_status()
+    back = back.cpu().numpy()
+    assert np.max(np.abs(back - c)) / np.max(np.abs(c)) < TOL
+
+
+def test_full_group_ragged_and_inverse_limits(su2):
     Ns = [64, 128, 64]
     rng = np.random.default_rng(73)
     grids = [_grid(n, rng) for n in Ns]
@@ -93,5 +127,5 @@ def test_full_group_ragged_and_forward_only(su2):
             j0, vals = T.forward_pair(g, 3, -5, full=True)
             got = np.array([o[OG.coeff_index(j0 + 2 * i, -5, 3)] for i in range(len(vals))])
             assert _rel(got, vals) < TOL
-    with pytest.raises(su2.SU2Error):
+    with pytest.raises(su2.SU2Error):                 # synthesis on the full group: N = 128, 256
         plan.inverse(torch.zeros(plan.coeff_elems, dtype=torch.complex64, device="cuda"))
