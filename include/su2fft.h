@@ -135,10 +135,12 @@ typedef struct {
  * alpha_j = gamma_j = -pi + 2 pi j/(N-1), j = 0..N-1 (the last node, +pi,
  * repeats the first), beta_k unchanged; the forward transform carries the cell
  * (2 pi/(N-1))^2, prefactor 1/(2(N-1)^2).  Grids keep the N^3 layout.  The
- * repeated node is folded onto the first and the (N-1)-point DFTs are taken
- * as dense products, so stage 1 costs O(N^4) per function instead of
- * O(N^3 log N).  complex64, any supported N, forward transform only
- * (su2_inverse and su2_backward return SU2_ERR_UNSUPPORTED); combined with
+ * repeated node is folded onto the first; for N >= 64 the (N-1)-point DFTs are
+ * taken by Bluestein's chirp-z convolution (O(N^3 log N) per function), below
+ * as dense products.  complex64, any supported N for the forward transform;
+ * su2_inverse and su2_backward (synthesis and adjoint at every printed node,
+ * the repeated ones included; adjoint prefactor 1/(2(N-1)^2)) for plans whose
+ * bandwidths are all >= 64, else SU2_ERR_UNSUPPORTED; combined with
  * SU2_FLAG_FULL_GROUP it is SU2_ERR_INVALID_ARG. */
 #define SU2_FLAG_LITERAL_GRID 0x8u
 

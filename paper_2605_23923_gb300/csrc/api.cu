@@ -1043,7 +1043,9 @@ static su2_status run_transpose(su2_plan_t plan, su2::TransposeMode mode, const 
                                 void* ws, void* stream) {
     su2_status s = check_exec(plan, coeffs, grid, ws);
     if (s != SU2_OK) return s;
-    if (plan->flags & SU2_FLAG_LITERAL_GRID) return SU2_ERR_UNSUPPORTED;   // printed grid: forward only
+    if (plan->flags & SU2_FLAG_LITERAL_GRID)                               // printed grid: N >= 64
+        for (const auto& kv : plan->bands)
+            if (!su2::fft_literal_bluestein(kv.first)) return SU2_ERR_UNSUPPORTED;
     if (plan->flags & SU2_FLAG_FULL_GROUP)                                 // full group: N = 128, 256
         for (const auto& kv : plan->bands)
             if ((kv.first != 128 && kv.first != 256) || kv.second.aux_ring <= 0) return SU2_ERR_UNSUPPORTED;

@@ -503,7 +503,7 @@ struct RecFF {
 // range (one broadcast row per l).  No d values are stored.  Output: the
 // workspace planes tile-major, [s][mi][ni/4][k][ni%4], so that the two
 // threads of a node group write one 32-byte sector and a warp 512 bytes.
-// Synthesis at N >= 256: the warps whose 32 nodes lie within N/8 of a pole
+// Synthesis at N >= 128: the warps whose 32 nodes lie within N/8 of a pole
 // run the recurrence in float-float (RecFF, coefficients with their low
 // parts); there the FP32 recurrence loses ~1e-4 of d at high l, which the
 // synthesis (weight 2l + 1, no sin(beta) factor) would show.
@@ -515,7 +515,7 @@ template <int N> struct Cfg {
     static constexpr int NODES = THREADS;                     // nodes per pass (2 per node group)
     static constexpr int PASSES = N / NODES;
     static constexpr int RS = N / 2;
-    static constexpr bool FF_POLES = N >= 256;                // float-float chains near the poles (synthesis)
+    static constexpr bool FF_POLES = N >= 128;                // float-float chains near the poles (synthesis)
     static constexpr size_t smem_bytes() {
         return sizeof(StepCoef<float>) * NB * RS + sizeof(float2) * RS * NB * BT + sizeof(SeedPair) * NB + 16 * NB +
                (FF_POLES ? sizeof(float2) * NB * RS : 0);
@@ -523,7 +523,7 @@ template <int N> struct Cfg {
 };
 }  // namespace tr32
 
-// FF: instantiation for the synthesis at N >= 256 (float-float chains near the
+// FF: instantiation for the synthesis at N >= 128 (float-float chains near the
 // poles); the adjoint and smaller N use the plain one, whose register count
 // stays unaffected.
 template <int N, bool FF>
@@ -584,8 +584,9 @@ contract_tr32(BandArgs a, int mode, const float2* __restrict__ coeffs, float2* _
     const StepCoef<float>* c0p = coef + (2 * h) * RS;
     const StepCoef<float>* c1p = coef + (2 * h + 1) * RS;
     // adjoint prefactor: the grid cell over the Haar measure, 1/(2N^2) on the paper's
-    // domain, 1/(4N^2) on the full group (psi over 4 pi)
-    const float inv2n2 = 1.f / ((a.full_group ? 4.f : 2.f) * (float)N * (float)N);
+    // domain, 1/(4N^2) on the full group (psi over 4 pi), 1/(2(N-1)^2) on the printed grid
+    const float NC = a.literal ? (float)(N - 1) : (float)N;
+    const float inv2n2 = 1.f / ((a.full_group ? 4.f : 2.f) * NC * NC);
     const int ni0 = tl.nb * NB + 2 * h;
 
     for (int pass = 0; pass < P::PASSES; ++pass) {

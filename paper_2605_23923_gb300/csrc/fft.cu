@@ -925,6 +925,7 @@ cudaError_t launch_fft_forward(const BandArgs& a, bool fp64, const void* grid, v
 }
 
 cudaError_t launch_fft_inverse(const BandArgs& a, bool fp64, const void* ws, void* grid, cudaStream_t st) {
+    if (a.literal) return fp64 ? cudaErrorInvalidValue : launch_fft_inverse_literal(a, ws, grid, st);
     if (a.full_group)                   // two-phase only (N = 128, 256; the caller checks)
         return (a.aux_ring > 0 && !fp64) ? launch_fft_inverse_two_phase(a, ws, grid, st) : cudaErrorInvalidValue;
     if (a.aux_ring > 0 && a.ws_tile_major && fft_inverse_two_phase_supported(a.N, fp64))

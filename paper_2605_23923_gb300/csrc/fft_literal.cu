@@ -237,14 +237,16 @@ namespace litbs {
 // Table block (float2 each): chirp_in[2][N] (sector 0: e^{i pi t^2/M}; sector 1:
 // e^{i pi (t^2 + t)/M}), chirp_out[N] (e^{i pi q^2/M}, q = c - N/2), filter[L]
 // (FFT of the chirp e^{-i pi u^2/M} over one period of L, divided by L, stored in
-// the order the forward four-step FFT leaves its output), om[L] (e^{2 pi i t/L}).
+// the order the forward four-step FFT leaves its output), om[L] (e^{2 pi i t/L}),
+// filter_inv[L] (the same for the chirp e^{+i pi u^2/M} on the inverse's range
+// of u; the inverse's chirps are the conjugates of chirp_out and chirp_in).
 template <int N> struct Cfg {
     static constexpr int M = N - 1, L = 2 * N;
     static constexpr int R1 = Radix<L>::R1, R2 = Radix<L>::R2;
     static constexpr int ROWS = N >= 512 ? 8 : 16;       // rows (launch 1) / columns (launch 2) per item
     static constexpr int PITCH = L + L / R1;             // one pad element per R1 block
     static constexpr int THREADS = 256;
-    static constexpr int TAB = 3 * N + 2 * L;
+    static constexpr int TAB = 3 * N + 3 * L;
     static constexpr size_t smem_bytes() { return (size_t)ROWS * PITCH * 8 + (size_t)ROWS * N * 8 + (size_t)TAB * 8; }
     __host__ __device__ static constexpr int pad(int p) { return p + p / R1; }
 };
@@ -409,6 +411,117 @@ lit_cols(BandArgs a, float2* __restrict__ ws, int p0) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Synthesis / adjoint on the printed grid: from the tile-major planes G_s[k][mi][ni]
+// (the transposed contraction's output) to the grid at every printed node,
+//   f[j1,k,j2] = sum_s sum_{n', m'} sg_s G_s e^{-2 pi i (n' j1 + m' j2)/M} e^{-i pi s (j1 + j2)/M}
+// for j1, j2 < M (n' = n or n0, the N frequencies of each angle, sg_s the origin
+// phase as in the forward), and at the repeated node +pi (j = M) the value at
+// -pi with the half-integer sector negated.  The inverse M-point DFTs (N inputs,
+// M outputs) by Bluestein with the conjugate chirps and the inverse filter.
+// Launch 1: plane, sector, 16 rows mi: DFT over ni -> T_s[mi][j1];
+// launch 2: plane, 16 columns j1, both sectors: DFT over mi, untwist, sector
+// sum, the repeated gamma node; the item of column j1 = 0 also writes row M.
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::THREADS)
+lit_inv_rows(BandArgs a, float2* __restrict__ ws, int p0) {
+    using P = Cfg<N>;
+    constexpr int M = P::M, L = P::L, NRB = N / P::ROWS;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2* buf = reinterpret_cast<float2*>(smem);                        // [ROWS][PITCH]
+    const float2* tab = load_tables<N>(a, smem, (size_t)P::ROWS * P::PITCH * 8);
+    __syncthreads();
+    const float2 *cin = tab, *cout = tab + 2 * N, *om = tab + 3 * N + L, *filt = tab + 3 * N + 2 * L;
+    const int plane = p0 + blockIdx.x / (2 * NRB), s = (blockIdx.x / NRB) & 1, rb = blockIdx.x % NRB;
+    const int fb = plane / N, k = plane % N;
+    const float2* G = ws + a.ws_off[a.fidx[fb]] + (size_t)s * N * N * N + (size_t)4 * k;
+    for (int e = threadIdx.x; e < P::ROWS * L; e += P::THREADS) {
+        const int rr = e / L, ni = e % L, mi = rb * P::ROWS + rr;
+        float2 v = make_float2(0.f, 0.f);
+        if (ni < N && !(s == 0 && (ni == 0 || mi == 0))) {
+            const float2 g = G[(size_t)mi * N * N + (size_t)(ni >> 2) * 4 * N + (ni & 3)];
+            float sg = ((ni + mi) & 1) ? -1.f : 1.f;
+            if (s) sg = -sg;
+            v = cmul(make_float2(g.x * sg, g.y * sg), cconj(cout[ni]));
+        }
+        buf[rr * P::PITCH + P::pad(ni)] = v;
+    }
+    __syncthreads();
+    conv_rows<N>(buf, filt, om);
+    float2* T = ws + a.ws_aux_off + ((size_t)(plane - p0) * 2 + s) * N * N;
+    for (int e = threadIdx.x; e < P::ROWS * N; e += P::THREADS) {
+        const int rr = e / N, j1 = e % N, mi = rb * P::ROWS + rr;
+        if (j1 >= M) continue;
+        T[(size_t)mi * N + j1] = cmul(buf[rr * P::PITCH + P::pad(j1 + N / 2)], cconj(cin[s * N + j1]));
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::THREADS)
+lit_inv_cols(BandArgs a, const float2* __restrict__ ws, float2* __restrict__ grid, int p0) {
+    using P = Cfg<N>;
+    constexpr int M = P::M, L = P::L, NCB = N / P::ROWS, R = P::ROWS;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2* buf = reinterpret_cast<float2*>(smem);                        // [ROWS][PITCH]
+    float2* Z = buf + R * P::PITCH;                                       // [ROWS][N] sector-0 values
+    const float2* tab = load_tables<N>(a, smem, (size_t)R * P::PITCH * 8 + (size_t)R * N * 8);
+    __syncthreads();
+    const float2 *cin = tab, *cout = tab + 2 * N, *om = tab + 3 * N + L, *filt = tab + 3 * N + 2 * L;
+    const int plane = p0 + blockIdx.x / NCB, cb = blockIdx.x % NCB;
+    const int fb = plane / N, k = plane % N;
+    float2* g = grid + a.grid_off[a.fidx[fb]] + (size_t)k * N;          // g[j1 N^2 + j2]
+    const size_t rs = (size_t)N * N;
+#pragma unroll 1
+    for (int s = 0; s < 2; ++s) {
+        const float2* T = ws + a.ws_aux_off + ((size_t)(plane - p0) * 2 + s) * N * N;
+        for (int e = threadIdx.x; e < R * L; e += P::THREADS) {
+            const int cc = e % R, mi = e / R, j1 = cb * R + cc;           // R consecutive j1 of row mi
+            float2 v = make_float2(0.f, 0.f);
+            if (mi < N && j1 < M) v = cmul(T[(size_t)mi * N + j1], cconj(cout[mi]));
+            buf[cc * P::PITCH + P::pad(mi)] = v;
+        }
+        __syncthreads();
+        conv_rows<N>(buf, filt, om);
+        for (int e = threadIdx.x; e < R * N; e += P::THREADS) {
+            const int cc = e / N, j2 = e % N, j1 = cb * R + cc;
+            if (j1 >= M || j2 >= M) continue;
+            const float2 y = cmul(buf[cc * P::PITCH + P::pad(j2 + N / 2)], cconj(cin[s * N + j2]));
+            if (s == 0) {
+                Z[cc * N + j2] = y;
+                continue;
+            }
+            const float2 z = Z[cc * N + j2];
+            g[(size_t)j1 * rs + j2] = make_float2(z.x + y.x, z.y + y.y);
+            if (j2 == 0) g[(size_t)j1 * rs + M] = make_float2(z.x - y.x, z.y - y.y);   // gamma = +pi
+            if (j1 == 0) {                                                          // alpha = +pi
+                g[(size_t)M * rs + j2] = make_float2(z.x - y.x, z.y - y.y);
+                if (j2 == 0) g[(size_t)M * rs + M] = make_float2(z.x + y.x, z.y + y.y);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int N>
+static cudaError_t launch_inv_n(const BandArgs& a, const void* ws, void* grid, cudaStream_t st) {
+    using P = Cfg<N>;
+    const size_t smem1 = (size_t)P::ROWS * P::PITCH * 8 + (size_t)P::TAB * 8;
+    const size_t smem2 = (size_t)P::ROWS * P::PITCH * 8 + (size_t)P::ROWS * N * 8 + (size_t)P::TAB * 8;
+    cudaError_t e = cudaFuncSetAttribute(lit_inv_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(lit_inv_cols<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+    if (e != cudaSuccess) return e;
+    const int nplanes = a.nfunc * N, chunk = a.aux_ring;
+    for (int p0 = 0; p0 < nplanes; p0 += chunk) {
+        const int np = nplanes - p0 < chunk ? nplanes - p0 : chunk;
+        lit_inv_rows<N><<<np * 2 * (N / P::ROWS), P::THREADS, smem1, st>>>(a, (float2*)ws, p0);
+        lit_inv_cols<N><<<np * (N / P::ROWS), P::THREADS, smem2, st>>>(a, (const float2*)ws, (float2*)grid, p0);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 // planes per chunk: the chunk's intermediate (2 N^2 complex per plane) stays
 // near 64 MB, well inside the L2
 inline int chunk_planes(int N) {
@@ -457,35 +570,43 @@ void fft_literal_bluestein_tables(int N, std::vector<float2>& out) {
         const double ang = pi * (double)r / (double)den;
         return make_float2((float)cos(ang), (float)sin(ang));
     };
-    out.assign(3 * N + 2 * L, make_float2(0.f, 0.f));
+    out.assign(3 * N + 3 * L, make_float2(0.f, 0.f));
     for (int t = 0; t < N; ++t) {
         out[t] = cis((long)t * t, M);
         out[N + t] = cis((long)t * t + t, M);
         const long q = t - N / 2;
         out[2 * N + t] = cis(q * q, M);
     }
-    // chirp e^{-i pi u^2/M} on u in [-N/2 - M + 1, N/2 - 1], placed at u mod L
-    std::vector<double> br(L, 0.0), bi(L, 0.0);
-    for (long u = -(long)(N / 2) - M + 1; u <= N / 2 - 1; ++u) {
-        long r = (u * u) % (2L * M);
-        const double ang = -pi * (double)r / (double)M;
-        const int idx = (int)((u % L + L) % L);
-        br[idx] = cos(ang);
-        bi[idx] = sin(ang);
-    }
-    for (int qa = 0; qa < R1; ++qa)
-        for (int qq = 0; qq < R2; ++qq) {
-            const int f = qq + R2 * qa;                  // frequency held at position qa + R1 qq
-            double sr = 0.0, si = 0.0;
-            for (int n = 0; n < L; ++n) {                // forward transform, e^{-2 pi i f n/L}
-                const long r = ((long)f * n) % L;
-                const double ang = -2.0 * pi * (double)r / (double)L;
-                const double c = cos(ang), sn = sin(ang);
-                sr += br[n] * c - bi[n] * sn;
-                si += br[n] * sn + bi[n] * c;
-            }
-            out[3 * N + qa + R1 * qq] = make_float2((float)(sr / L), (float)(si / L));
+    // filter spectra: the chirp e^{sg i pi u^2/M} on u in [u0, u1], placed at u mod L,
+    // transformed (e^{-2 pi i f n/L}), divided by L, in the four-step output order
+    auto filter = [&](double sg, long u0, long u1, int at) {
+        std::vector<double> br(L, 0.0), bi(L, 0.0);
+        for (long u = u0; u <= u1; ++u) {
+            const long r = (u * u) % (2L * M);
+            const double ang = sg * pi * (double)r / (double)M;
+            const int idx = (int)((u % L + L) % L);
+            br[idx] = cos(ang);
+            bi[idx] = sin(ang);
         }
+        for (int qa = 0; qa < R1; ++qa)
+            for (int qq = 0; qq < R2; ++qq) {
+                const int f = qq + R2 * qa;              // frequency held at position qa + R1 qq
+                double sr = 0.0, si = 0.0;
+                for (int n = 0; n < L; ++n) {
+                    const long r = ((long)f * n) % L;
+                    const double ang = -2.0 * pi * (double)r / (double)L;
+                    const double c = cos(ang), sn = sin(ang);
+                    sr += br[n] * c - bi[n] * sn;
+                    si += br[n] * sn + bi[n] * c;
+                }
+                out[at + qa + R1 * qq] = make_float2((float)(sr / L), (float)(si / L));
+            }
+    };
+    // forward: outputs q in [-N/2, N/2 - 1] from inputs t in [0, M): u = q - t
+    filter(-1.0, -(long)(N / 2) - M + 1, N / 2 - 1, 3 * N);
+    // inverse: outputs j in [0, M) from inputs q in [-N/2, N/2 - 1] at position q + N/2:
+    // u = j + N/2 - p ranges over [-N/2 + 1, 3N/2 - 2]
+    filter(1.0, -(long)(N / 2) + 1, 3L * N / 2 - 2, 3 * N + 2 * L);
     for (int t = 0; t < L; ++t) {
         const double ang = 2.0 * pi * (double)t / (double)L;
         out[3 * N + L + t] = make_float2((float)cos(ang), (float)sin(ang));
@@ -509,6 +630,18 @@ cudaError_t fft_forward_literal_aux(int N, int device, int* ctas, size_t* elems)
     // one N x N slab per CTA, rounded to 256 bytes (32 complex64)
     *elems = (((size_t)*ctas * N * N + 31) / 32) * 32;
     return cudaSuccess;
+}
+
+cudaError_t launch_fft_inverse_literal(const BandArgs& a, const void* ws, void* grid, cudaStream_t st) {
+    if (a.nfunc <= 0) return cudaSuccess;
+    if (!fft_literal_bluestein(a.N) || a.aux_ring < 1 || !a.lit_bs || !a.ws_tile_major) return cudaErrorInvalidValue;
+    switch (a.N) {
+        case 64: return litbs::launch_inv_n<64>(a, ws, grid, st);
+        case 128: return litbs::launch_inv_n<128>(a, ws, grid, st);
+        case 256: return litbs::launch_inv_n<256>(a, ws, grid, st);
+        case 512: return litbs::launch_inv_n<512>(a, ws, grid, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_fft_forward_literal(const BandArgs& a, const void* grid, void* ws, cudaStream_t st) {

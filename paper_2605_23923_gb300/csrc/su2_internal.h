@@ -28,6 +28,8 @@ cudaError_t fft_forward_literal_aux(int N, int device, int* ctas, size_t* elems)
 bool fft_literal_bluestein(int N);
 void fft_literal_bluestein_tables(int N, std::vector<float2>& out);
 cudaError_t launch_fft_forward_literal(const BandArgs& a, const void* grid, void* ws, cudaStream_t st);
+// Synthesis / adjoint grid from the tile-major planes on the printed grid (N >= 64).
+cudaError_t launch_fft_inverse_literal(const BandArgs& a, const void* ws, void* grid, cudaStream_t st);
 // Two-phase complex64 inverse DFT (N = 128, 256, 512) over the tile-major
 // planes, using the forward's scratch ring.
 bool fft_inverse_two_phase_supported(int N, bool fp64);

@@ -2,9 +2,10 @@
 2 pi/(N-1), the node +pi repeating -pi, prefactor 1/(2(N-1)^2)) against the
 oracle's same sum: whole grids at N = 4..64 with both beta weightings and both
 contraction paths, sampled pairs at N = 128 and 256, a ragged batch, grids
-whose repeated nodes disagree (the fold must add them, not pick one), and the
-forward-only restriction.  Tolerance 1e-5 relative to the largest oracle
-coefficient, as for the other complex64 tests."""
+whose repeated nodes disagree (the fold must add them, not pick one); the
+synthesis and the adjoint at every printed node (the repeated ones included)
+at N = 64 and 128, and their restriction to N >= 64.  Tolerance 1e-5 relative
+to the largest oracle value, as for the other complex64 tests."""
 import numpy as np
 import pytest
 
@@ -95,12 +96,48 @@ def test_literal_sampled(su2, N, algo):
     assert worst / scale < TOL
 
 
-def test_literal_ragged_and_forward_only(su2):
+@pytest.mark.parametrize("N,algo", [(64, "fp32"), (64, "tc_bf16x3"), (128, "fp32")])
+def test_literal_inverse_and_adjoint(su2, N, algo):
+    """Synthesis (Sec. 3 expansion) and the adjoint of the printed-grid forward
+    map at every node of the printed grid, two functions, against the oracle."""
+    B = 2
+    rng = np.random.default_rng(94 + N)
+    cs = [I.draw_coeffs(N, rng, "inv1").astype(np.complex64) for _ in range(B)]
+    plan = su2.Plan(N=N, batch=B, dtype="c64", algo=algo, literal=True)
+    c_dev = torch.from_numpy(np.concatenate(cs)).cuda()
+    syn = plan.inverse(c_dev).cpu().numpy().astype(np.complex128)
+    adj = plan.backward(c_dev).cpu().numpy().astype(np.complex128)
+    plan.sync_status()
+    for b in range(B):
+        o = plan.grid_offsets[b]
+        c64 = cs[b].astype(np.complex128)
+        got_s = syn[o:o + N ** 3].reshape(N, N, N)
+        got_a = adj[o:o + N ** 3].reshape(N, N, N)
+        assert _rel(got_s, T.inverse_separable(c64, N, literal=True)) < TOL, ("synthesis", b)
+        assert _rel(got_a, T.adjoint_separable(c64, N, literal=True)) < TOL, ("adjoint", b)
+
+
+def test_literal_adjoint_identity_n256(su2):
+    """<A f, g> = <f, A^H g> on the printed grid at N = 256 (any size)."""
+    N = 256
+    plan = su2.Plan(N=N, batch=1, dtype="c64", algo="tc_bf16x3", literal=True)
+    gen = torch.Generator(device="cuda").manual_seed(95)
+    f = torch.randn(plan.grid_elems, dtype=torch.complex64, device="cuda", generator=gen)
+    g = torch.randn(plan.coeff_elems, dtype=torch.complex64, device="cuda", generator=gen)
+    af = plan.forward(f)
+    lhs = torch.vdot(af.to(torch.complex128), g.to(torch.complex128))
+    rhs = torch.vdot(f.to(torch.complex128), plan.backward(g).to(torch.complex128))
+    plan.sync_status()
+    scale = (af.abs().double().norm() * g.abs().double().norm()).item()
+    assert abs((lhs - rhs).item()) < TOL * scale
+
+
+def test_literal_ragged_and_inverse_limits(su2):
     Ns = [16, 64, 32, 16]
     rng = np.random.default_rng(93)
     grids = [_grid(n, rng) for n in Ns]
     plan, outs = _run(su2, grids, Ns, "tc_bf16x3")
     for g, o in zip(grids, outs):
         assert _rel(o, T.forward_separable(g, literal=True)) < TOL
-    with pytest.raises(su2.SU2Error):
+    with pytest.raises(su2.SU2Error):                 # synthesis on the printed grid: N >= 64
         plan.inverse(torch.zeros(plan.coeff_elems, dtype=torch.complex64, device="cuda"))
