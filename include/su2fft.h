@@ -143,6 +143,22 @@ typedef struct {
  * bandwidths are all >= 64, else SU2_ERR_UNSUPPORTED; combined with
  * SU2_FLAG_FULL_GROUP it is SU2_ERR_INVALID_ARG. */
 #define SU2_FLAG_LITERAL_GRID 0x8u
+/* SU2_FLAG_PERSISTENT: su2_forward runs the whole forward transform of every
+ * function (stage 1 and stage 2 of Sec. 6, every bandwidth group) as one
+ * persistent kernel launch (after a memset of its counters in the workspace):
+ * one thread block per SM takes items in order from a work list (stage-1 DFTs
+ * of a few beta planes of one function, then FP32 contraction tiles, then
+ * tensor-core contraction tiles); a contraction item waits, with a bounded
+ * spin that latches SU2_ERR_TIMEOUT, until the stage-1 items of its block of
+ * functions are done.  Only for complex64 plans on the periodic grid whose
+ * bandwidths are all in {8, 16, 32, 64, 128} (tensor-core groups: 64, 128),
+ * else su2_plan returns SU2_ERR_UNSUPPORTED.  Without this flag, a plan that
+ * qualifies and is created with SU2_FLAG_AUTOTUNE times the whole forward
+ * both ways (on scratch buffers of its size, when they fit in half the free
+ * device memory) and keeps the faster; other plans launch each group's two
+ * stages separately.  su2_forward_stage1 / su2_forward_stage2 and
+ * su2_forward_pipelined always run per group. */
+#define SU2_FLAG_PERSISTENT 0x10u
 
 /* Supported bandwidths: N a power of two with 4 <= N <= 512 (c64) and
  * 4 <= N <= 256 (c128).  Anything else returns SU2_ERR_UNSUPPORTED. */
@@ -155,9 +171,15 @@ su2_status su2_plan(su2_plan_t* out, const su2_plan_desc* desc);
 /* Bytes of device workspace that su2_forward / su2_inverse / su2_backward
  * need: the stage-1 planes of every function (2 N^3 complex each), followed,
  * for complex64 bandwidths N = 128, 256, 512, by scratch of the forward 2-D DFT
- * (a ring of intermediate planes and its counters; tens of MB per bandwidth).
+ * (a ring of intermediate planes and its counters; tens of MB per bandwidth),
+ * and, for plans created with SU2_FLAG_PERSISTENT or SU2_FLAG_AUTOTUNE whose
+ * bandwidths qualify for the persistent launch, that launch's counters (a few
+ * bytes per 32 functions).
  * The content is undefined between calls and needs no initialisation. */
 su2_status su2_workspace_size(su2_plan_t plan, size_t* bytes);
+/* *used = 1 when su2_forward runs the persistent launch of SU2_FLAG_PERSISTENT
+ * (set by that flag or chosen by SU2_FLAG_AUTOTUNE), else 0. */
+su2_status su2_plan_persistent(su2_plan_t plan, int* used);
 /* (The environment variable SU2_STAGE1_MAX_CTAS, if set to n >= 1, caps the
  * grid of that forward 2-D DFT at n thread blocks; it exists to check that the
  * kernel completes with any number of resident blocks.  Results do not change.) */

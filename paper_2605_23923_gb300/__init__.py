@@ -41,7 +41,8 @@ class Plan:
 
     def __init__(self, N=None, batch: int = 1, dtype: str = "c64", algo: str = "auto",
                  weights: str = "cc", device: int | None = None, Ns=None, graph: bool = False,
-                 autotune: bool = False, full_group: bool = False, literal: bool = False):
+                 autotune: bool = False, full_group: bool = False, literal: bool = False,
+                 persistent: bool = False):
         self._lib = load()
         if Ns is not None:
             Ns = [int(n) for n in Ns]
@@ -65,7 +66,8 @@ class Plan:
         desc.algo = _abi.ALGOS[algo]
         desc.weights = _abi.WEIGHTS[weights]
         desc.flags = ((_abi.FLAG_CUDA_GRAPH if graph else 0) | (_abi.FLAG_AUTOTUNE if autotune else 0) |
-                      (_abi.FLAG_FULL_GROUP if full_group else 0) | (_abi.FLAG_LITERAL_GRID if literal else 0))
+                      (_abi.FLAG_FULL_GROUP if full_group else 0) | (_abi.FLAG_LITERAL_GRID if literal else 0) |
+                      (_abi.FLAG_PERSISTENT if persistent else 0))
         self.full_group = full_group
         self.literal = literal
         desc.device = self.device
@@ -75,6 +77,9 @@ class Plan:
         sz = ctypes.c_size_t()
         _abi.check("su2_workspace_size", self._lib.su2_workspace_size(h, ctypes.byref(sz)))
         self.workspace_bytes = int(sz.value)
+        used = ctypes.c_int()
+        _abi.check("su2_plan_persistent", self._lib.su2_plan_persistent(h, ctypes.byref(used)))
+        self.persistent = bool(used.value)      # su2_forward runs the one-launch path
         ge, ce = ctypes.c_size_t(), ctypes.c_size_t()
         _abi.check("su2_grid_elems", self._lib.su2_grid_elems(h, ctypes.byref(ge)))
         _abi.check("su2_coeff_elems", self._lib.su2_coeff_elems(h, ctypes.byref(ce)))

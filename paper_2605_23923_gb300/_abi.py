@@ -47,10 +47,12 @@ FLAG_CUDA_GRAPH = 0x1
 FLAG_AUTOTUNE = 0x2
 FLAG_FULL_GROUP = 0x4
 FLAG_LITERAL_GRID = 0x8
+FLAG_PERSISTENT = 0x10
 
 SIGNATURES = [
     ("su2_plan", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(PlanDesc)]),
     ("su2_workspace_size", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    ("su2_plan_persistent", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     ("su2_grid_offset", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
     ("su2_coeff_offset", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
     ("su2_plane_offset", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),

@@ -155,6 +155,15 @@ struct su2_plan_s {
         cudaGraphExec_t exec;
     };
     std::vector<GraphEntry> graphs;   // most recent last
+    // the whole forward as one persistent launch (ragged.cu): every group fits it
+    // (rg_ok), su2_forward runs it (rg_use); its counters sit in the workspace
+    bool rg_ok = false, rg_use = false;
+    std::vector<su2::RaggedBand> rg_bands;
+    su2::RaggedBand* d_rg_bands = nullptr;
+    int4* d_rg_items = nullptr;
+    int rg_nitems = 0, rg_nctr = 0;
+    size_t rg_ctr_off = 0;            // in complex elements from the workspace start
+    int lf2_len = 0;
 
     template <typename T>
     cudaError_t upload(T** dst, const T* src, size_t count) {
@@ -345,7 +354,16 @@ cudaError_t launch_band_forward(const su2_plan_s* P, const Band& b, const void* 
 
 // Every group's forward transform; with several groups they run concurrently
 // on the plan's streams, forked from and joined back into `st`.
+// The forward transform as one persistent launch over every group (ragged.cu).
+cudaError_t launch_ragged_plan(const su2_plan_s* P, const void* grid, void* coeffs, void* ws, cudaStream_t st) {
+    const size_t esz = sizeof(float2);
+    unsigned* ctr = reinterpret_cast<unsigned*>(static_cast<char*>(ws) + P->rg_ctr_off * esz);
+    return su2::launch_ragged(P->rg_bands, P->d_rg_bands, P->d_rg_items, P->rg_nitems, ctr, P->rg_nctr, P->d_lf2,
+                              P->lf2_len, P->d_err, grid, ws, coeffs, st);
+}
+
 cudaError_t enqueue_forward(su2_plan_s* P, const void* grid, void* coeffs, void* ws, cudaStream_t st) {
+    if (P->rg_use) return launch_ragged_plan(P, grid, coeffs, ws, st);
     if (P->band_streams.empty()) {
         for (auto& kv : P->bands) {
             const cudaError_t e = launch_band_forward(P, kv.second, grid, coeffs, ws, st);
@@ -592,6 +610,9 @@ void apply_choice(Band& b, const TuneChoice& c) {
 // contraction with each stage-1 variant (two-phase; the DSMEM cluster one at
 // N = 64, 128) and each FP32 form (row classes; 8 or 16 functions per block) --
 // and keep the fastest.  Results do not depend on the choice.
+cudaError_t build_ragged(su2_plan_s* P);
+cudaError_t autotune_ragged(su2_plan_s* P, std::map<std::string, TuneChoice>& cache, bool* dirty);
+
 cudaError_t autotune(su2_plan_s* P) {
     if (P->dtype != SU2_C64) return cudaSuccess;
     const char* cache_path = getenv("SU2_TUNE_CACHE");
@@ -700,8 +721,78 @@ cudaError_t autotune(su2_plan_s* P) {
         }
     }
     cudaStreamDestroy(st);
+    if (e == cudaSuccess && P->rg_ok) e = build_ragged(P);
+    if (e == cudaSuccess && P->rg_ok && !(P->flags & SU2_FLAG_PERSISTENT) && P->bands.size() > 1)
+        e = autotune_ragged(P, cache, &cache_dirty);
     if (e == cudaSuccess && cache_dirty) write_tune_cache(cache_path, cache);
     return e;
+}
+
+// Work list and group table of the persistent launch, from the groups' final
+// contraction choices; leaves rg_ok false when a group does not fit it.
+cudaError_t build_ragged(su2_plan_s* P) {
+    P->rg_bands.clear();
+    for (auto& kv : P->bands) {
+        su2::RaggedBand rb;
+        memset(&rb, 0, sizeof(rb));
+        rb.a = band_args(P, kv.second);
+        rb.tc = kv.second.tc ? 1 : 0;
+        if (!su2::ragged_supported(kv.first, rb.tc != 0)) {
+            P->rg_ok = false;
+            return cudaSuccess;
+        }
+        P->rg_bands.push_back(rb);
+    }
+    std::vector<int4> items;
+    su2::ragged_items(P->rg_bands, items, &P->rg_nctr);
+    P->rg_nitems = (int)items.size();
+    cudaError_t e = P->upload(&P->d_rg_bands, P->rg_bands.data(), P->rg_bands.size());
+    if (e == cudaSuccess) e = P->upload(&P->d_rg_items, items.data(), items.size());
+    return e;
+}
+
+// Persistent launch or one launch pair per group on forked streams: time the
+// whole forward both ways on scratch buffers of the plan's size (when they fit
+// in half the free memory) and keep the faster.  The cache key is the plan's
+// bandwidth multiset.
+cudaError_t autotune_ragged(su2_plan_s* P, std::map<std::string, TuneChoice>& cache, bool* dirty) {
+    std::string key = tune_key(P, 0, P->B) + "|ragged";
+    for (auto& kv : P->bands) key += "|" + std::to_string(kv.first) + "x" + std::to_string(kv.second.fids.size()) +
+                                     (kv.second.tc ? "t" : "f");
+    auto hit = cache.find(key);
+    if (hit != cache.end()) {
+        P->rg_use = hit->second.tc != 0;
+        return cudaSuccess;
+    }
+    size_t free_b = 0, total_b = 0;
+    cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
+    if (e != cudaSuccess) return e;
+    const size_t need = (P->grid_total + P->coeff_total + P->ws_total) * sizeof(float2);
+    if (need > free_b / 2) return cudaSuccess;          // keep the default
+    void *dg = nullptr, *dc = nullptr, *dw = nullptr;
+    cudaStream_t st = nullptr;
+    e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&dg, P->grid_total * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc(&dc, P->coeff_total * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc(&dw, P->ws_total * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMemsetAsync(dg, 0, P->grid_total * sizeof(float2), st);
+    float ms[2] = {1e30f, 1e30f};
+    for (int use = 0; use < 2 && e == cudaSuccess; ++use) {
+        P->rg_use = use != 0;
+        e = time_ms(st, &ms[use], [&]() { return enqueue_forward(P, dg, dc, dw, st); });
+    }
+    if (st) cudaStreamSynchronize(st);
+    if (dg) cudaFree(dg);
+    if (dc) cudaFree(dc);
+    if (dw) cudaFree(dw);
+    if (st) cudaStreamDestroy(st);
+    if (e != cudaSuccess) return e;
+    P->rg_use = ms[1] < ms[0];
+    TuneChoice c;
+    c.tc = P->rg_use ? 1 : 0;
+    cache[key] = c;
+    *dirty = true;
+    return cudaSuccess;
 }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
@@ -750,7 +841,8 @@ const char* su2_status_string(su2_status s) {
 su2_status su2_plan(su2_plan_t* out, const su2_plan_desc* desc) {
     if (!out || !desc) return SU2_ERR_INVALID_ARG;
     if (desc->num_functions < 1 ||
-        (desc->flags & ~(SU2_FLAG_CUDA_GRAPH | SU2_FLAG_AUTOTUNE | SU2_FLAG_FULL_GROUP | SU2_FLAG_LITERAL_GRID)) != 0)
+        (desc->flags & ~(SU2_FLAG_CUDA_GRAPH | SU2_FLAG_AUTOTUNE | SU2_FLAG_FULL_GROUP | SU2_FLAG_LITERAL_GRID |
+                         SU2_FLAG_PERSISTENT)) != 0)
         return SU2_ERR_INVALID_ARG;
     const bool full_group = (desc->flags & SU2_FLAG_FULL_GROUP) != 0;
     const bool literal = (desc->flags & SU2_FLAG_LITERAL_GRID) != 0;
@@ -848,7 +940,26 @@ su2_status su2_plan(su2_plan_t* out, const su2_plan_desc* desc) {
         kv.second.full_group = full_group;
         P->ws_total += elems;
     }
+    // completion counters of the persistent launch (ragged.cu), sized for the
+    // smallest function block any contraction choice uses; only plans that ask
+    // for it or may choose it (autotuner) carry them
+    P->rg_ok = desc->dtype == SU2_C64 && !full_group && !literal &&
+               (desc->flags & (SU2_FLAG_PERSISTENT | SU2_FLAG_AUTOTUNE)) != 0;
+    for (auto& kv : P->bands)
+        if (!su2::ragged_supported(kv.first, false)) P->rg_ok = false;
+    if (P->rg_ok) {
+        size_t blocks = 0;
+        for (auto& kv : P->bands)
+            blocks += (kv.second.fids.size() + su2::ragged_min_block() - 1) / su2::ragged_min_block();
+        P->rg_ctr_off = P->ws_total;
+        P->ws_total += ((1 + blocks) * sizeof(unsigned) + sizeof(float2) - 1) / sizeof(float2);
+    }
+    if ((desc->flags & SU2_FLAG_PERSISTENT) && !P->rg_ok) {
+        delete P;
+        return SU2_ERR_UNSUPPORTED;
+    }
     std::vector<double> lf2(2 * Nmax + 2);
+    P->lf2_len = (int)lf2.size();
     for (size_t k = 0; k < lf2.size(); ++k) lf2[k] = lgamma((double)k + 1.0) / log(2.0);
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = P->upload(&P->d_grid_off, P->grid_off.data(), P->B);
@@ -879,12 +990,27 @@ su2_status su2_plan(su2_plan_t* out, const su2_plan_desc* desc) {
     if (e == cudaSuccess && (P->flags & SU2_FLAG_CUDA_GRAPH))
         e = cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess && (P->flags & SU2_FLAG_AUTOTUNE)) e = autotune(P);
+    else if (e == cudaSuccess && P->rg_ok) e = build_ragged(P);
+    if (e == cudaSuccess && (P->flags & SU2_FLAG_PERSISTENT)) {
+        if (!P->rg_ok) {
+            P->release();
+            delete P;
+            return SU2_ERR_UNSUPPORTED;
+        }
+        P->rg_use = true;
+    }
     if (e != cudaSuccess) {
         P->release();
         delete P;
         return from_cuda(e);
     }
     *out = P;
+    return SU2_OK;
+}
+
+su2_status su2_plan_persistent(su2_plan_t plan, int* used) {
+    if (!plan || !used) return SU2_ERR_INVALID_ARG;
+    *used = plan->rg_use ? 1 : 0;
     return SU2_OK;
 }
 

@@ -61,6 +61,38 @@ bool tc_supported(int N);
 bool encode_tensor_map_8b(CUtensorMap* map, int rank, const void* base, const cuuint64_t* dims,
                           const cuuint64_t* strides_bytes, const cuuint32_t* box);
 
+// One bandwidth group of the ragged-batch kernel (one persistent launch over
+// every group; ragged.cu).
+struct RaggedBand {
+    BandArgs a;          // the group's arguments (tables, offsets, plane layout)
+    int tc;              // 1: contraction on tensor cores (tile-major planes)
+    int fblk;            // functions per block (completion counters, contraction items)
+    int nblk;            // blocks of the group
+    int s1pf;            // stage-1 items per function
+    int cbase;           // first completion counter of the group's blocks
+    int tcmap;           // tensor map of the group's planes (tensor-core groups), else -1
+    int tab;             // first entry of the group's node tables in shared memory
+    // stage-1 items of block bb (functions bb*fblk .. min(nfunc, (bb+1)*fblk) - 1)
+    __host__ __device__ int s1_per_block(int bb) const {
+        const int rest = a.nfunc - bb * fblk;
+        return (rest < fblk ? rest : fblk) * s1pf;
+    }
+};
+// Bandwidths the ragged kernel takes (tensor-core groups: 64 and 128).
+bool ragged_supported(int N, bool tc);
+// Functions per block of a group, and the smallest over all groups (for sizing
+// the completion counters before the contraction choice is final).
+int ragged_block(int N, bool tc);
+int ragged_min_block();
+// Fills cbase, fblk, nblk, s1pf, tcmap, tab of the groups and builds the work
+// list; *nctr = counters the launch uses (item counter + one per block).
+void ragged_items(std::vector<RaggedBand>& bands, std::vector<int4>& items, int* nctr);
+// The launch: zeroes the nctr counters at ctr (in the workspace), encodes the
+// tensor maps of the tensor-core groups' planes, and runs the kernel on `st`.
+cudaError_t launch_ragged(const std::vector<RaggedBand>& hb, const RaggedBand* d_bands, const int4* d_items,
+                          int nitems, unsigned* ctr, int nctr, const double* lf2, int lf2_len, int* err,
+                          const void* grid, void* ws, void* coeffs, cudaStream_t st);
+
 // Device ordinal a plan's tables live on.
 int plan_device(const su2_plan_s* plan);
 // su2_forward's checks and launches, always enqueued launch by launch (never

@@ -96,7 +96,8 @@ def test_graph_replay_follows_new_inputs(su2, algo):
 def test_ragged_tensor_core_autotune_and_cache(su2, tmp_path, monkeypatch):
     """A tensor-core plan over the ragged batch with the autotuner (which may move
     a group to the FP32 contraction) against the oracle-checked plain plan; the
-    choices go to the SU2_TUNE_CACHE file, and a second plan that reads them
+    choices (per group, and one-launch or per-group launches for the whole
+    plan) go to the SU2_TUNE_CACHE file, and a second plan that reads them
     gives the same coefficients bit for bit."""
     import json
     cache = tmp_path / "tune.json"
@@ -113,10 +114,13 @@ def test_ragged_tensor_core_autotune_and_cache(su2, tmp_path, monkeypatch):
     d = (out - ref).abs().max().item() / ref.abs().max().item()
     assert d < TOL, d
     entries = json.loads(cache.read_text())
-    assert len(entries) == 4                          # one per bandwidth group
+    # one per bandwidth group, and the whole plan's persistent-launch choice
+    assert len(entries) == 5
+    assert sum("|ragged|" in k for k in entries) == 1
     for v in entries.values():
         assert set(v) == {"tc", "s1", "rc", "bt"}
     again = su2.Plan(Ns=Ns, dtype="c64", algo="tc_bf16x3", autotune=True)
+    assert again.persistent == plan.persistent
     out2 = again.forward(x)
     again.sync_status()
     assert torch.equal(out2, out)
