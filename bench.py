@@ -355,7 +355,8 @@ def secondary_workloads(su2, I, torch, dev, stream, peaks, fp32_peak):
     gen = torch.Generator(device=dev)
     gen.manual_seed(3)
     rag = {"workload": "512 functions, N drawn uniformly from {16,32,64,128} (seed 3), complex64, "
-                       "seeded white-noise grids; one CUDA-graph launch per forward, autotuned kernels",
+                       "seeded white-noise grids; one CUDA-graph launch per forward, autotuned kernels (and the "
+                       "choice between one persistent launch and per-group launches); both forms also timed forced",
            "n_by_band": {str(n): int((Ns == n).sum()) for n in (16, 32, 64, 128)}}
     for algo in ("tc_bf16x3", "fp32"):
         plan = su2.Plan(Ns=Ns, dtype="c64", algo=algo, graph=True, autotune=True)
@@ -364,8 +365,18 @@ def secondary_workloads(su2, I, torch, dev, stream, peaks, fp32_peak):
         ws = plan.workspace()
         ms = _time_ms(torch, stream, lambda: plan.forward(x, out=y, ws=ws, stream=stream), steps=10)
         plan.sync_status()
-        rag[algo] = {"ms_per_forward": ms, "FFTs/s": 512 / ms * 1e3}
+        rag[algo] = {"ms_per_forward": ms, "FFTs/s": 512 / ms * 1e3,
+                     "autotuner_chose": "one persistent launch" if plan.persistent else "per-group launches"}
         plan.close()
+        # both forms forced, each recorded in a CUDA graph
+        for pers in (True, False):
+            p2 = su2.Plan(Ns=Ns, dtype="c64", algo=algo, graph=True, persistent=pers)
+            ws2 = p2.workspace()
+            ms2 = _time_ms(torch, stream, lambda: p2.forward(x, out=y, ws=ws2, stream=stream), steps=10)
+            p2.sync_status()
+            rag[algo]["persistent_ms" if pers else "per_group_ms"] = ms2
+            p2.close()
+            del ws2
         del x, y, ws
         torch.cuda.empty_cache()
     out["ragged_512"] = rag
