@@ -248,12 +248,23 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const __
                     tma_store_5d(&omap, src + h * P::BOXR * W, ni0, h * P::BOXR, ob.s, k, fb, pol);
             }
             bulk_commit();
-            bulk_wait_read_all();          // the slot may be refilled once the box is read
         };
         int n = 0;
         for (;;) {
             // Items are handed out in number order, so every item this CTA waits
             // on below is already held by a running CTA (no residency assumption).
+            // Per item: once the slot is released, the staged output block of the
+            // B item it held goes out by tensor stores (not waited for here), then
+            // the next item number is taken and its dependency waited on while the
+            // stores read the slot; the read is waited for just before the refill.
+            const int b = n % NS;
+            const unsigned u = (unsigned)(n / NS);
+            ++n;
+            bool stop = u > 0 && !mbar_wait_bounded(&empty[b], (u - 1) & 1, a.err);
+            if (lane == 0 && pend(b) >= 0) {
+                store_block(pend(b), S + b * P::SLOTP);
+                pend(b) = -1;
+            }
             int i = 0;
             if (lane == 0) {
                 do {
@@ -261,14 +272,8 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const __
                 } while (i < nitems && !decode<N>(i, nplanes, D).valid);
             }
             i = __shfl_sync(0xffffffffu, i, 0);
-            const int b = n % NS;
-            const unsigned u = (unsigned)(n / NS);
-            ++n;
-            if (u > 0 && !mbar_wait_bounded(&empty[b], (u - 1) & 1, a.err)) i = nitems;
-            if (lane == 0 && pend(b) >= 0) {
-                store_block(pend(b), S + b * P::SLOTP);
-                pend(b) = -1;
-            }
+            if (stop) i = nitems;
+            if (i >= nitems && lane == 0) bulk_wait_read_all();
             if (i >= nitems) {
                 if (lane == 0) {
                     slot_item[b] = -1;
@@ -297,6 +302,7 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const __
                 constexpr int GN = FULL ? 2 * N : N;              // psi nodes of a grid row
                 if (a.grid_regular) {
                     if (lane == 0) {
+                        bulk_wait_read_all();          // the slot's staged block has been read
                         mbar_arrive_expect_tx(&full[b], (uint32_t)(NSL * SLOT * 8));
 #pragma unroll
                         for (int sl = 0; sl < NSL; ++sl)
@@ -318,6 +324,7 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const __
                     }
                 } else {
                     const float2* src = grid + a.grid_off[a.fidx[fb]] + (size_t)k * GN + it.jb * W;
+                    if (lane == 0) bulk_wait_read_all();
                     if (lane == 0) mbar_arrive_expect_tx(&full[b], (uint32_t)(NSL * SLOT * 8));
                     __syncwarp();
                     for (int sl = 0; sl < NSL; ++sl)
@@ -331,6 +338,7 @@ fft_fwd_two_phase(BandArgs a, const __grid_constant__ CUtensorMap gmap, const __
                 // are done, so the compute warps never wait on L2 latency themselves.
                 wait_counter_bounded(&doneA[r], (use + 1) * P::NA, a.err);
                 fence_proxy_async_global();          // the acquire above orders the copy's reads
+                bulk_wait_read_all();                // the slot's staged block has been read
                 mbar_arrive_expect_tx(&full[b], (uint32_t)(SLOT * 8));
                 bulk_g2s(dst, ring + ((size_t)(r * 2 + it.s) * N + it.pb * W) * N, (uint32_t)(SLOT * 8), &full[b]);
             }
