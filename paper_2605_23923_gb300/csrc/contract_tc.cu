@@ -13,21 +13,23 @@
 //
 // One persistent CTA per SM owns tiles of 4 consecutive n at fixed
 // (sector, m) and 64 functions.  Warp roles, connected by mbarriers:
-//   warp 0      TMA: F2 chunk [64 functions][16 nodes][4 n] into a ring of four
+//   warp 0      TMA: F2 chunk [64 functions][16 nodes][4 n] into a ring of three
 //               stages (the planes are tile-major, so a function's chunk is 512 B)
 //   warp 1      MMA issue (one thread), tensor-memory owner
 //   warps 2-5, 10-11  convert a landed F2 chunk (fp32) into the BF16 hi/lo A
 //               operands in place: all of it is read into registers, the six
 //               warps meet at a named barrier, then the operands are written
 //               over the same 32 KB (hi and lo of 4 pairs fill it exactly)
-//   warps 6-9   two generator groups (even / odd chunks): the d-values of the
-//               4 pairs x 16 nodes by the three-term recurrence, written as the
-//               BF16 hi/lo B operands
+//   warps 6-9, 16-17  three generator groups (chunks g = 0, 1, 2 mod 3): the
+//               d-values of the 4 pairs x 16 nodes by the three-term recurrence,
+//               written as the BF16 hi/lo B operands
 //   warps 12-15 epilogue: tensor memory -> i^{n-m} * coefficients
-// Four stages of F2 / A (a stage is reloaded once the MMAs that read it are
-// done), two of B; the MMA commits free them.  With the operands converted in
-// place the TMA can run up to three chunks (96 KB) ahead of the MMAs, which
-// covers the DRAM latency at this kernel's share of the bandwidth.
+// Three stages of F2 / A (a stage is reloaded once the MMAs that read it are
+// done) and three of B, one per generator group; the MMA commits free them.
+// The recurrence is the critical path: each chunk's MMAs wait for its d-values,
+// and a group can start its next chunk only once the MMAs of its previous one
+// are done, so the number of groups (bounded by the B stages that fit in
+// shared memory) sets the rate.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -43,14 +45,18 @@ namespace tc {
 constexpr int RMAX = 128;                   // rows of l per pair (N <= 256)
 constexpr int NMAX = 256;
 
+constexpr int NSK = 3;                      // F2 / A stages of this kernel
+constexpr int NGRP = 3;                     // generator groups = B stages
+constexpr int W_GEN3 = 16;                  // warps 16-17: the third generator group
+constexpr int THREADS_K = (NWARPS + 2) * 32;
 constexpr int OFF_STG = 0;                  // stage st at OFF_STG + st * SA (F2, then its A operands)
-constexpr int OFF_B = OFF_STG + NSA * SA;
-constexpr int OFF_COEF = OFF_B + 2 * B_BYTES;
-constexpr int OFF_TAB = OFF_COEF + 2 * NP * RMAX * (int)sizeof(StepCoef<float>);
+constexpr int OFF_B = OFF_STG + NSK * SA;
+constexpr int OFF_COEF = OFF_B + NGRP * B_BYTES;
+constexpr int OFF_TAB = OFF_COEF + NGRP * NP * RMAX * (int)sizeof(StepCoef<float>);
 // seed32 (float4) + lf2 (double) + xsplit (float2) + seed parameters of the pairs
-constexpr int TAB_BYTES = NMAX * 16 + NMAX * 8 + NMAX * 8 + 2 * NP * (int)sizeof(SeedPair) + NMAX * 4;
+constexpr int TAB_BYTES = NMAX * 16 + NMAX * 8 + NMAX * 8 + NGRP * NP * (int)sizeof(SeedPair) + NMAX * 4;
 constexpr int OFF_BAR = OFF_TAB + TAB_BYTES;
-constexpr int NBAR = 4 * NSA + 2 * 2 + 4;
+constexpr int NBAR = 3 * NSK + 2 * NGRP + 4;
 constexpr int SMEM_BYTES = OFF_BAR + NBAR * 8 + 16;
 static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 constexpr uint32_t TMEM_COLS = 512;         // 4 pairs x 128 columns, or two halves of 4 x 64
@@ -66,28 +72,28 @@ __device__ __forceinline__ void acc_place(int nmma, int& nexth, int& h0, bool& b
 }
 
 template <int N>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(THREADS_K, 1)
 contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2* __restrict__ coeffs) {
     extern __shared__ __align__(1024) unsigned char smem[];
     constexpr int NCH = N / KC;
-    static_assert(NCH % 2 == 0, "even number of chunks: a generator group keeps its stage");
+
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OFF_BAR);
-    uint64_t* bar_full = bars + 0;               // [NSA] TMA landed              (count 1 + tx)
-    uint64_t* bar_afull = bars + NSA;            // [NSA] A operands written      (count N_CONV)
-    uint64_t* bar_opa = bars + 2 * NSA;          // [NSA] MMAs of the A stage done (tcgen05.commit)
-    uint64_t* bar_bfull = bars + 3 * NSA;        // [2] B operands written        (count 2)
-    uint64_t* bar_opb = bars + 3 * NSA + 2;      // [2] MMAs of the B stage done  (tcgen05.commit)
-    uint64_t* bar_accfull = bars + 3 * NSA + 4;  // [2] accumulators of a tile in half h final (tcgen05.commit)
-    uint64_t* bar_hfree = bars + 3 * NSA + 6;    // [2] epilogue drained half h    (count 4)
+    uint64_t* bar_full = bars + 0;               // [NSK] TMA landed              (count 1 + tx)
+    uint64_t* bar_afull = bars + NSK;            // [NSK] A operands written      (count N_CONV)
+    uint64_t* bar_opa = bars + 2 * NSK;          // [NSK] MMAs of the A stage done (tcgen05.commit)
+    uint64_t* bar_bfull = bars + 3 * NSK;        // [NGRP] B operands written     (count 2)
+    uint64_t* bar_opb = bar_bfull + NGRP;        // [NGRP] MMAs of the B stage done (tcgen05.commit)
+    uint64_t* bar_accfull = bar_opb + NGRP;      // [2] accumulators of a tile in half h final (tcgen05.commit)
+    uint64_t* bar_hfree = bar_accfull + 2;       // [2] epilogue drained half h    (count 4)
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + NBAR);
     float4* t_seed = reinterpret_cast<float4*>(smem + OFF_TAB);
     double* t_lf2 = reinterpret_cast<double*>(t_seed + NMAX);
     float2* t_xs = reinterpret_cast<float2*>(t_lf2 + NMAX);
-    SeedPair* t_gp = reinterpret_cast<SeedPair*>(t_xs + NMAX);      // [2 groups][NP]
-    uint32_t* t_rowoff = reinterpret_cast<uint32_t*>(t_gp + 2 * NP); // J(J+1)(2J+1)/6, J = 2l
+    SeedPair* t_gp = reinterpret_cast<SeedPair*>(t_xs + NMAX);      // [NGRP groups][NP]
+    uint32_t* t_rowoff = reinterpret_cast<uint32_t*>(t_gp + NGRP * NP); // J(J+1)(2J+1)/6, J = 2l
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    for (int t = tid; t < N; t += THREADS) {
+    for (int t = tid; t < N; t += THREADS_K) {
         t_seed[t] = a.seed32[t];
         t_lf2[t] = a.lf2[t];
         t_xs[t] = a.xsplit[t];
@@ -99,12 +105,12 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        for (int i = 0; i < NSA; ++i) {
+        for (int i = 0; i < NSK; ++i) {
             mbar_init(&bar_full[i], 1);
             mbar_init(&bar_afull[i], N_CONV);
             mbar_init(&bar_opa[i], 1);
         }
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < NGRP; ++i) {
             mbar_init(&bar_bfull[i], 2);
             mbar_init(&bar_opb[i], 1);
         }
@@ -137,8 +143,8 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
                 if (!tl.any) continue;
                 const int bb = item % nbb;
                 for (int c = 0; c < NCH; ++c, ++g) {
-                    const int st = g % NSA;
-                    const uint32_t u = g / NSA;
+                    const int st = g % NSK;
+                    const uint32_t u = g / NSK;
                     if (u > 0) mbar_wait_bounded(&bar_opa[st], (u - 1) & 1, a.err);   // its A operands read
                     mbar_arrive_expect_tx(&bar_full[st], (uint32_t)STAGE_BYTES);
                     if (a.xrecv) {        // [source][row][fb][n/4][node][n%4], nk nodes per source
@@ -176,9 +182,9 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
                 const uint32_t pstride = big ? 128u : 64u;
                 tc_fence_after();
                 for (int c = 0; c < NCH; ++c, ++g) {
-                    const int sa = g % NSA, sb = g & 1;
-                    mbar_wait_bounded(&bar_afull[sa], (g / NSA) & 1, a.err);
-                    mbar_wait_bounded(&bar_bfull[sb], (g >> 1) & 1, a.err);
+                    const int sa = g % NSK, sb = g % NGRP;
+                    mbar_wait_bounded(&bar_afull[sa], (g / NSK) & 1, a.err);
+                    mbar_wait_bounded(&bar_bfull[sb], (g / NGRP) & 1, a.err);
                     tc_fence_after();
                     unsigned char* Ab = smem + OFF_STG + sa * SA;
                     unsigned char* Bb = smem + OFF_B + sb * B_BYTES;
@@ -217,8 +223,8 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
             tl.decode(N, a.tc_t0 + item / nbb);
             if (!tl.any) continue;
             for (int c = 0; c < NCH; ++c, ++g) {
-                const int st = g % NSA;
-                mbar_wait_bounded(&bar_full[st], (g / NSA) & 1, a.err);   // stage free: TMA waited for the MMAs
+                const int st = g % NSK;
+                mbar_wait_bounded(&bar_full[st], (g / NSK) & 1, a.err);   // stage free: TMA waited for the MMAs
                 const float2* stg = reinterpret_cast<const float2*>(smem + OFF_STG + st * SA);
                 unsigned char* Ab = smem + OFF_STG + st * SA;
                 // every converter reads its items of the staged chunk before any of
@@ -256,7 +262,7 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
                 if (lane == 0) mbar_arrive(&bar_afull[st]);
             }
         }
-    } else if (warp >= W_GEN && warp < W_GEN + 4) {
+    } else if ((warp >= W_GEN && warp < W_GEN + 4) || warp == W_GEN3 || warp == W_GEN3 + 1) {
         // ------------------------------------------------------------------ recurrence -> B (bf16 hi/lo)
         // Thread (p, kk) runs the chain of pair p at node c*KC + kk/4 + 4*(kk%4) (K
         // position kk, the order the converters use) for the chunks of
@@ -266,8 +272,8 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
         // below 2^-39 and enters as 0.  A warp whose chains all have E = 0 runs the
         // plain recurrence; otherwise cur is renormalised once per 8 rows when
         // |cur| >= 2^40 (8 steps grow it by less than 2^41, so it stays finite).
-        const int grp = (warp - W_GEN) >> 1;               // handles the chunks of stage grp
-        const int gt = tid - W_GEN * 32 - grp * 64;        // 0..63
+        const int grp = warp >= W_GEN3 ? 2 : (warp - W_GEN) >> 1;   // handles the chunks of stage grp
+        const int gt = tid - (warp >= W_GEN3 ? W_GEN3 * 32 : W_GEN * 32 + grp * 64);   // 0..63
         const int p = gt >> 4, kk = gt & 15;
         StepCoef<float>* coef = reinterpret_cast<StepCoef<float>*>(smem + OFF_COEF) + grp * NP * RMAX;
         SeedPair* gp = t_gp + grp * NP;
@@ -277,22 +283,22 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
             tl.decode(N, a.tc_t0 + item / nbb);
             if (!tl.any) continue;
             const int Lt = tl.L, nmma = (Lt + 15) & ~15;
-            named_sync(1 + grp, 64);                       // previous tile's tables no longer read
+            named_sync(grp == 2 ? 4 : 1 + grp, 64);        // previous tile's tables no longer read
             for (int idx = gt; idx < NP * (Lt - 1); idx += 64) {
                 const int pp = idx % NP, r = idx / NP;
                 const int J = tl.j0 + 2 * r;
                 if (J >= tl.mu2[pp]) coef[pp * RMAX + r] = step_coef<float>(J, tl.n2[pp], tl.m2);
             }
             if (gt < NP) gp[gt] = make_seed_pair(t_lf2, tl.n2[gt], tl.m2);
-            named_sync(1 + grp, 64);
+            named_sync(grp == 2 ? 4 : 1 + grp, 64);
             const bool valid = tl.valid[p];
             const int rp = valid ? (tl.mu2[p] - tl.j0) / 2 : nmma;   // first row of my pair
             const SeedPair q = gp[p];
             const StepCoef<float>* cp = coef + p * RMAX;
             for (int c = 0; c < NCH; ++c, ++g) {
-                const int st = g & 1;
+                const int st = g % NGRP;
                 if (st != grp) continue;
-                const uint32_t u = g >> 1;
+                const uint32_t u = g / NGRP;
                 if (u > 0) mbar_wait_bounded(&bar_opb[st], (u - 1) & 1, a.err);
                 unsigned char* Bh = smem + OFF_B + st * B_BYTES + p * OPB + (kk >> 3) * LBO_B + (kk & 7) * 16;
                 unsigned char* Bl = Bh + NP * OPB;
@@ -520,7 +526,7 @@ static cudaError_t launch_n(const BandArgs& a, const void* ws, void* coeffs, cud
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int nitems = (a.tc_ntiles ? a.tc_ntiles : 2 * N * (N / NP)) * ((a.nfunc + BM - 1) / BM);
     const int grid = sms < nitems ? sms : nitems;
-    kern<<<grid, THREADS, SMEM_BYTES, st>>>(a, map, (float2*)coeffs);
+    kern<<<grid, THREADS_K, SMEM_BYTES, st>>>(a, map, (float2*)coeffs);
     return cudaGetLastError();
 }
 
