@@ -13,19 +13,20 @@
 //
 // One persistent CTA per SM owns tiles of 4 consecutive n at fixed
 // (sector, m) and 64 functions.  Warp roles, connected by mbarriers:
-//   warp 0      TMA: F2 chunk [64 functions][16 nodes][4 n] into a ring of three
+//   warp 0      TMA: F2 chunk [64 functions][16 nodes][4 n] into the ring of F2 / A
 //               stages (the planes are tile-major, so a function's chunk is 512 B)
 //   warp 1      MMA issue (one thread), tensor-memory owner
 //   warps 2-5, 10-11  convert a landed F2 chunk (fp32) into the BF16 hi/lo A
 //               operands in place: all of it is read into registers, the six
 //               warps meet at a named barrier, then the operands are written
 //               over the same 32 KB (hi and lo of 4 pairs fill it exactly)
-//   warps 6-9, 16-17  three generator groups (chunks g = 0, 1, 2 mod 3): the
-//               d-values of the 4 pairs x 16 nodes by the three-term recurrence,
-//               written as the BF16 hi/lo B operands
+//   warps 6-9 (and 16-17 at N = 256)  two (three) generator groups, chunk g to
+//               group g mod 2 (3): the d-values of the 4 pairs x 16 nodes by the
+//               three-term recurrence, written as the BF16 hi/lo B operands
 //   warps 12-15 epilogue: tensor memory -> i^{n-m} * coefficients
-// Three stages of F2 / A (a stage is reloaded once the MMAs that read it are
-// done) and three of B, one per generator group; the MMA commits free them.
+// Four (three at N = 256) stages of F2 / A (a stage is reloaded once the MMAs
+// that read it are done) and one B stage per generator group; the MMA commits
+// free them.
 // The recurrence is the critical path: each chunk's MMAs wait for its d-values,
 // and a group can start its next chunk only once the MMAs of its previous one
 // are done, so the number of groups (bounded by the B stages that fit in
@@ -45,20 +46,28 @@ namespace tc {
 constexpr int RMAX = 128;                   // rows of l per pair (N <= 256)
 constexpr int NMAX = 256;
 
-constexpr int NSK = 3;                      // F2 / A stages of this kernel
-constexpr int NGRP = 3;                     // generator groups = B stages
-constexpr int W_GEN3 = 16;                  // warps 16-17: the third generator group
-constexpr int THREADS_K = (NWARPS + 2) * 32;
-constexpr int OFF_STG = 0;                  // stage st at OFF_STG + st * SA (F2, then its A operands)
-constexpr int OFF_B = OFF_STG + NSK * SA;
-constexpr int OFF_COEF = OFF_B + NGRP * B_BYTES;
-constexpr int OFF_TAB = OFF_COEF + NGRP * NP * RMAX * (int)sizeof(StepCoef<float>);
-// seed32 (float4) + lf2 (double) + xsplit (float2) + seed parameters of the pairs
-constexpr int TAB_BYTES = NMAX * 16 + NMAX * 8 + NMAX * 8 + NGRP * NP * (int)sizeof(SeedPair) + NMAX * 4;
-constexpr int OFF_BAR = OFF_TAB + TAB_BYTES;
-constexpr int NBAR = 3 * NSK + 2 * NGRP + 4;
-constexpr int SMEM_BYTES = OFF_BAR + NBAR * 8 + 16;
-static_assert(SMEM_BYTES <= 232448, "shared memory budget");
+constexpr int W_GEN3 = 16;                  // warps 16-17: the third generator group (N = 256)
+// Shared-memory layout for NG generator groups (= B stages): three at N = 256,
+// where the recurrence over up to 128 rows of l is the critical path, two
+// (with a fourth F2 / A stage) at N <= 128, where a third group's warps only
+// take issue slots from the others (measured: N = 256 x 64 6.76 -> 6.12 ms,
+// N = 128 x 64 0.75 -> 0.85 ms with three).
+template <int NG>
+struct Lay {
+    static constexpr int NSK = NG == 3 ? 3 : 4;        // F2 / A stages
+    static constexpr int THREADS = (NWARPS + 2 * (NG - 2)) * 32;
+    static constexpr int OFF_STG = 0;                  // stage st at OFF_STG + st * SA (F2, then its A operands)
+    static constexpr int OFF_B = OFF_STG + NSK * SA;
+    static constexpr int OFF_COEF = OFF_B + NG * B_BYTES;
+    static constexpr int OFF_TAB = OFF_COEF + NG * NP * RMAX * (int)sizeof(StepCoef<float>);
+    // seed32 (float4) + lf2 (double) + xsplit (float2) + seed parameters of the pairs
+    static constexpr int TAB_BYTES = NMAX * 16 + NMAX * 8 + NMAX * 8 + NG * NP * (int)sizeof(SeedPair) + NMAX * 4;
+    static constexpr int OFF_BAR = OFF_TAB + TAB_BYTES;
+    static constexpr int NBAR = 3 * NSK + 2 * NG + 4;
+    static constexpr int SMEM_BYTES = OFF_BAR + NBAR * 8 + 16;
+    static_assert(SMEM_BYTES <= 232448, "shared memory budget");
+};
+template <int N> constexpr int ngroups() { return N >= 256 ? 3 : 2; }
 constexpr uint32_t TMEM_COLS = 512;         // 4 pairs x 128 columns, or two halves of 4 x 64
 // Accumulator placement: a tile with at most 64 rows of l ("small") takes one
 // half of tensor memory (pairs 64 columns apart), alternating halves, so its
@@ -72,8 +81,12 @@ __device__ __forceinline__ void acc_place(int nmma, int& nexth, int& h0, bool& b
 }
 
 template <int N>
-__global__ void __launch_bounds__(THREADS_K, 1)
+__global__ void __launch_bounds__(Lay<ngroups<N>()>::THREADS, 1)
 contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2* __restrict__ coeffs) {
+    constexpr int NGRP = ngroups<N>();
+    using L = Lay<NGRP>;
+    constexpr int NSK = L::NSK, THREADS_K = L::THREADS, OFF_STG = L::OFF_STG, OFF_B = L::OFF_B,
+                  OFF_COEF = L::OFF_COEF, OFF_TAB = L::OFF_TAB, OFF_BAR = L::OFF_BAR, NBAR = L::NBAR;
     extern __shared__ __align__(1024) unsigned char smem[];
     constexpr int NCH = N / KC;
 
@@ -518,15 +531,16 @@ static cudaError_t launch_n(const BandArgs& a, const void* ws, void* coeffs, cud
         const void* base = (const char*)ws + a.ws_group_off * sizeof(float2);
         if (!encode_tensor_map_8b(&map, 5, base, dims, strides, box)) return cudaErrorNotSupported;
     }
+    using L = Lay<ngroups<N>()>;
     auto kern = contract_tc_kernel<N>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int nitems = (a.tc_ntiles ? a.tc_ntiles : 2 * N * (N / NP)) * ((a.nfunc + BM - 1) / BM);
     const int grid = sms < nitems ? sms : nitems;
-    kern<<<grid, THREADS_K, SMEM_BYTES, st>>>(a, map, (float2*)coeffs);
+    kern<<<grid, L::THREADS, L::SMEM_BYTES, st>>>(a, map, (float2*)coeffs);
     return cudaGetLastError();
 }
 
