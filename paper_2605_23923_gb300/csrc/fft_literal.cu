@@ -247,7 +247,11 @@ template <int N> struct Cfg {
     static constexpr int PITCH = L + L / R1;             // one pad element per R1 block
     static constexpr int THREADS = 256;
     static constexpr int TAB = 3 * N + 3 * L;
-    static constexpr size_t smem_bytes() { return (size_t)ROWS * PITCH * 8 + (size_t)ROWS * N * 8 + (size_t)TAB * 8; }
+    // launch 1 keeps its raw input rows in shared memory below N = 256; from 256 on
+    // it rereads them from L2 for the second sector instead, so that two blocks fit
+    // per SM (N = 256 x 8: 10.4 -> 9.5 ms; at N = 128 three fit either way)
+    static constexpr bool RAW = N < 256;
+    static constexpr size_t smem_bytes() { return (size_t)ROWS * PITCH * 8 + (RAW ? (size_t)ROWS * N * 8 : 0) + (size_t)TAB * 8; }
     __host__ __device__ static constexpr int pad(int p) { return p + p / R1; }
 };
 
@@ -321,16 +325,18 @@ lit_rows(BandArgs a, const float2* __restrict__ grid, float2* __restrict__ ws, i
     constexpr int M = P::M, L = P::L, NRB = N / P::ROWS;
     extern __shared__ __align__(16) unsigned char smem[];
     float2* buf = reinterpret_cast<float2*>(smem);                        // [ROWS][PITCH]
-    float2* raw = buf + P::ROWS * P::PITCH;                               // [ROWS][N]
-    const float2* tab = load_tables<N>(a, smem, (size_t)P::ROWS * P::PITCH * 8 + (size_t)P::ROWS * N * 8);
+    float2* raw = buf + P::ROWS * P::PITCH;                               // [ROWS][N] (RAW)
+    const float2* tab = load_tables<N>(a, smem, (size_t)P::ROWS * P::PITCH * 8 + (P::RAW ? (size_t)P::ROWS * N * 8 : 0));
     const float2 *cin = tab, *cout = tab + 2 * N, *filt = tab + 3 * N, *om = filt + L;
     const int plane = p0 + blockIdx.x / NRB, rb = blockIdx.x % NRB;
     const int fb = plane / N, k = plane % N;
     const float2* g = grid + a.grid_off[a.fidx[fb]] + (size_t)k * N;     // plane k: g[j1 N^2 + j2]
     const size_t rs = (size_t)N * N;
-    for (int e = threadIdx.x; e < P::ROWS * N; e += P::THREADS) {
-        const int rr = e / N, t = e % N, j1 = rb * P::ROWS + rr;
-        raw[e] = (j1 < M) ? g[(size_t)j1 * rs + t] : make_float2(0.f, 0.f);
+    if constexpr (P::RAW) {
+        for (int e = threadIdx.x; e < P::ROWS * N; e += P::THREADS) {
+            const int rr = e / N, t = e % N, j1 = rb * P::ROWS + rr;
+            raw[e] = (j1 < M) ? g[(size_t)j1 * rs + t] : make_float2(0.f, 0.f);
+        }
     }
     __syncthreads();
     float2* T = ws + a.ws_aux_off + (size_t)(plane - p0) * 2 * N * N;
@@ -341,9 +347,9 @@ lit_rows(BandArgs a, const float2* __restrict__ grid, float2* __restrict__ ws, i
             const int rr = e / L, t = e % L, j1 = rb * P::ROWS + rr;
             float2 v = make_float2(0.f, 0.f);
             if (j1 < M && t < M) {
-                v = raw[rr * N + t];
+                v = P::RAW ? raw[rr * N + t] : __ldg(g + (size_t)j1 * rs + t);
                 if (t == 0) {                                  // repeated gamma node folded
-                    const float2 u = raw[rr * N + M];
+                    const float2 u = P::RAW ? raw[rr * N + M] : __ldg(g + (size_t)j1 * rs + M);
                     v.x += sg * u.x;
                     v.y += sg * u.y;
                 }
@@ -533,8 +539,8 @@ inline int chunk_planes(int N) {
 template <int N>
 static cudaError_t launch_n(const BandArgs& a, const void* grid, void* ws, cudaStream_t st) {
     using P = Cfg<N>;
-    // launch 1: rows + raw rows + tables; launch 2: rows + tables
-    const size_t smem1 = P::smem_bytes(), smem2 = P::smem_bytes() - (size_t)P::ROWS * N * 8;
+    // launch 1: rows (+ raw rows below N = 256) + tables; launch 2: rows + tables
+    const size_t smem2 = (size_t)P::ROWS * P::PITCH * 8 + (size_t)P::TAB * 8, smem1 = P::smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(lit_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(lit_cols<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
     if (e != cudaSuccess) return e;
