@@ -244,7 +244,9 @@ template <int N> struct Cfg {
     static constexpr int M = N - 1, L = 2 * N;
     static constexpr int R1 = Radix<L>::R1, R2 = Radix<L>::R2;
     static constexpr int ROWS = N >= 512 ? 8 : 16;       // rows (launch 1) / columns (launch 2) per item
-    static constexpr int PITCH = L + L / R1;             // one pad element per R1 block
+    // one pad element per R1 block, plus one so that the rows start in different
+    // banks (the column launches fill their rows across lanes)
+    static constexpr int PITCH = L + L / R1 + 1;
     static constexpr int THREADS = 256;
     static constexpr int TAB = 3 * N + 3 * L;
     // launch 1 keeps its raw input rows in shared memory below N = 256; from 256 on
