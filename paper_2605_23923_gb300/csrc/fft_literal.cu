@@ -249,11 +249,13 @@ template <int N> struct Cfg {
     static constexpr int PITCH = L + L / R1 + 1;
     static constexpr int THREADS = 256;
     static constexpr int TAB = 3 * N + 3 * L;
+    // in shared memory: the chirps (3N) and the re-laid filter and twiddles (3L)
+    static constexpr int TABX = 3 * N + 3 * L;
     // launch 1 keeps its raw input rows in shared memory below N = 256; from 256 on
     // it rereads them from L2 for the second sector instead, so that two blocks fit
     // per SM (N = 256 x 8: 10.4 -> 9.5 ms; at N = 128 three fit either way)
     static constexpr bool RAW = N < 256;
-    static constexpr size_t smem_bytes() { return (size_t)ROWS * PITCH * 8 + (RAW ? (size_t)ROWS * N * 8 : 0) + (size_t)TAB * 8; }
+    static constexpr size_t smem_bytes() { return (size_t)ROWS * PITCH * 8 + (RAW ? (size_t)ROWS * N * 8 : 0) + (size_t)TABX * 8; }
     __host__ __device__ static constexpr int pad(int p) { return p + p / R1; }
 };
 
@@ -262,8 +264,12 @@ template <int N> struct Cfg {
 // R1-point DFTs), filter, and the transposed steps backwards (inverse R1-point
 // DFTs, conjugate twiddle, inverse R2-point DFTs), so the permuted frequency
 // order of the forward FFT is never undone explicitly.
+// The filter and twiddles come re-laid so that consecutive lanes read consecutive
+// entries: filtT[qa R2 + qq] = filter[qa + R1 qq], omA[qq R1 + ia] = omB[ia R2 + qq]
+// = om[ia qq] (lanes vary ia in the R2-point passes, qq in the R1-point pass).
 template <int N>
-__device__ __forceinline__ void conv_rows(float2* buf, const float2* __restrict__ filt, const float2* __restrict__ om) {
+__device__ __forceinline__ void conv_rows(float2* buf, const float2* __restrict__ filtT, const float2* __restrict__ omA,
+                                          const float2* __restrict__ omB) {
     using P = Cfg<N>;
     constexpr int R1 = P::R1, R2 = P::R2;
     const int tid = threadIdx.x;
@@ -275,7 +281,7 @@ __device__ __forceinline__ void conv_rows(float2* buf, const float2* __restrict_
         for (int q = 0; q < R2; ++q) v[q] = x[P::pad(ia + R1 * q)];
         dft_reg<R2, -1, float>(v);
 #pragma unroll
-        for (int qq = 1; qq < R2; ++qq) v[qq] = cmul(v[qq], cconj(om[ia * qq]));
+        for (int qq = 1; qq < R2; ++qq) v[qq] = cmul(v[qq], cconj(omA[qq * R1 + ia]));
 #pragma unroll
         for (int qq = 0; qq < R2; ++qq) x[P::pad(ia + R1 * qq)] = v[qq];
     }
@@ -288,10 +294,10 @@ __device__ __forceinline__ void conv_rows(float2* buf, const float2* __restrict_
         for (int ia = 0; ia < R1; ++ia) v[ia] = x[ia];
         dft_reg<R1, -1, float>(v);                       // v[qa]: frequency qq + R2 qa
 #pragma unroll
-        for (int qa = 0; qa < R1; ++qa) v[qa] = cmul(v[qa], filt[qa + R1 * qq]);
+        for (int qa = 0; qa < R1; ++qa) v[qa] = cmul(v[qa], filtT[qa * R2 + qq]);
         dft_reg<R1, 1, float>(v);
 #pragma unroll
-        for (int ia = 1; ia < R1; ++ia) v[ia] = cmul(v[ia], om[ia * qq]);
+        for (int ia = 1; ia < R1; ++ia) v[ia] = cmul(v[ia], omB[ia * R2 + qq]);
 #pragma unroll
         for (int ia = 0; ia < R1; ++ia) x[ia] = v[ia];
     }
@@ -309,13 +315,24 @@ __device__ __forceinline__ void conv_rows(float2* buf, const float2* __restrict_
     __syncthreads();
 }
 
-// Copies the table block to shared memory at byte offset `off` (the caller
-// makes it visible with a barrier before the first use).
+// Copies the chirps of the table block to shared memory at byte offset `off`,
+// followed by the re-laid filter (the inverse's when inv) and twiddles that
+// conv_rows reads (the caller makes them visible with a barrier before the
+// first use).
 template <int N>
-__device__ __forceinline__ float2* load_tables(const BandArgs& a, unsigned char* smem, size_t off) {
+__device__ __forceinline__ float2* load_tables(const BandArgs& a, unsigned char* smem, size_t off, bool inv) {
     using P = Cfg<N>;
+    constexpr int L = P::L, R1 = P::R1, R2 = P::R2;
     float2* tab = reinterpret_cast<float2*>(smem + off);
-    for (int t = threadIdx.x; t < P::TAB; t += P::THREADS) tab[t] = a.lit_bs[t];
+    for (int t = threadIdx.x; t < 3 * N; t += P::THREADS) tab[t] = a.lit_bs[t];   // chirps
+    const float2* filt = a.lit_bs + 3 * N + (inv ? 2 * L : 0);
+    const float2* om = a.lit_bs + 3 * N + L;
+    float2* x = tab + 3 * N;                             // [filtT L][omA L][omB L]
+    for (int t = threadIdx.x; t < L; t += P::THREADS) {
+        x[t] = filt[(t / R2) + R1 * (t % R2)];           // filtT[qa R2 + qq]
+        x[L + t] = om[(t % R1) * (t / R1)];              // omA[qq R1 + ia]
+        x[2 * L + t] = om[(t / R2) * (t % R2)];          // omB[ia R2 + qq]
+    }
     return tab;
 }
 
@@ -328,8 +345,8 @@ lit_rows(BandArgs a, const float2* __restrict__ grid, float2* __restrict__ ws, i
     extern __shared__ __align__(16) unsigned char smem[];
     float2* buf = reinterpret_cast<float2*>(smem);                        // [ROWS][PITCH]
     float2* raw = buf + P::ROWS * P::PITCH;                               // [ROWS][N] (RAW)
-    const float2* tab = load_tables<N>(a, smem, (size_t)P::ROWS * P::PITCH * 8 + (P::RAW ? (size_t)P::ROWS * N * 8 : 0));
-    const float2 *cin = tab, *cout = tab + 2 * N, *filt = tab + 3 * N, *om = filt + L;
+    const float2* tab = load_tables<N>(a, smem, (size_t)P::ROWS * P::PITCH * 8 + (P::RAW ? (size_t)P::ROWS * N * 8 : 0), false);
+    const float2 *cin = tab, *cout = tab + 2 * N;
     const int plane = p0 + blockIdx.x / NRB, rb = blockIdx.x % NRB;
     const int fb = plane / N, k = plane % N;
     const float2* g = grid + a.grid_off[a.fidx[fb]] + (size_t)k * N;     // plane k: g[j1 N^2 + j2]
@@ -370,7 +387,7 @@ lit_rows(BandArgs a, const float2* __restrict__ grid, float2* __restrict__ ws, i
             buf[rr * P::PITCH + P::pad(t)] = v;
         }
         __syncthreads();
-        conv_rows<N>(buf, filt, om);
+        conv_rows<N>(buf, tab + 3 * N, tab + 3 * N + L, tab + 3 * N + 2 * L);
         for (int e = threadIdx.x; e < P::ROWS * N; e += P::THREADS) {
             const int rr = e / N, c = e % N, j1 = rb * P::ROWS + rr;
             if (j1 >= M) continue;
@@ -389,9 +406,9 @@ lit_cols(BandArgs a, float2* __restrict__ ws, int p0) {
     constexpr int M = P::M, L = P::L, NCB = N / P::ROWS, R = P::ROWS;
     extern __shared__ __align__(16) unsigned char smem[];
     float2* buf = reinterpret_cast<float2*>(smem);                        // [ROWS][PITCH]
-    const float2* tab = load_tables<N>(a, smem, (size_t)P::ROWS * P::PITCH * 8);   // no raw rows here
+    const float2* tab = load_tables<N>(a, smem, (size_t)P::ROWS * P::PITCH * 8, false);   // no raw rows here
     __syncthreads();
-    const float2 *cin = tab, *cout = tab + 2 * N, *filt = tab + 3 * N, *om = filt + L;
+    const float2 *cin = tab, *cout = tab + 2 * N;
     const int plane = p0 + blockIdx.x / (2 * NCB), s = (blockIdx.x / NCB) & 1, cb = blockIdx.x % NCB;
     const int fb = plane / N, k = plane % N;
     const float2* T = ws + a.ws_aux_off + ((size_t)(plane - p0) * 2 + s) * N * N;
@@ -402,7 +419,7 @@ lit_cols(BandArgs a, float2* __restrict__ ws, int p0) {
         buf[cc * P::PITCH + P::pad(j1)] = v;
     }
     __syncthreads();
-    conv_rows<N>(buf, filt, om);
+    conv_rows<N>(buf, tab + 3 * N, tab + 3 * N + L, tab + 3 * N + 2 * L);
     const float scale = a.w32[k] / (2.f * (float)M * (float)M);
     const size_t plane_off = a.ws_off[a.fidx[fb]];
     for (int e = threadIdx.x; e < R * N; e += P::THREADS) {
@@ -438,9 +455,9 @@ lit_inv_rows(BandArgs a, float2* __restrict__ ws, int p0) {
     constexpr int M = P::M, L = P::L, NRB = N / P::ROWS;
     extern __shared__ __align__(16) unsigned char smem[];
     float2* buf = reinterpret_cast<float2*>(smem);                        // [ROWS][PITCH]
-    const float2* tab = load_tables<N>(a, smem, (size_t)P::ROWS * P::PITCH * 8);
+    const float2* tab = load_tables<N>(a, smem, (size_t)P::ROWS * P::PITCH * 8, true);
     __syncthreads();
-    const float2 *cin = tab, *cout = tab + 2 * N, *om = tab + 3 * N + L, *filt = tab + 3 * N + 2 * L;
+    const float2 *cin = tab, *cout = tab + 2 * N;
     const int plane = p0 + blockIdx.x / (2 * NRB), s = (blockIdx.x / NRB) & 1, rb = blockIdx.x % NRB;
     const int fb = plane / N, k = plane % N;
     const float2* G = ws + a.ws_off[a.fidx[fb]] + (size_t)s * N * N * N + (size_t)4 * k;
@@ -456,7 +473,7 @@ lit_inv_rows(BandArgs a, float2* __restrict__ ws, int p0) {
         buf[rr * P::PITCH + P::pad(ni)] = v;
     }
     __syncthreads();
-    conv_rows<N>(buf, filt, om);
+    conv_rows<N>(buf, tab + 3 * N, tab + 3 * N + L, tab + 3 * N + 2 * L);
     float2* T = ws + a.ws_aux_off + ((size_t)(plane - p0) * 2 + s) * N * N;
     for (int e = threadIdx.x; e < P::ROWS * N; e += P::THREADS) {
         const int rr = e / N, j1 = e % N, mi = rb * P::ROWS + rr;
@@ -473,9 +490,9 @@ lit_inv_cols(BandArgs a, const float2* __restrict__ ws, float2* __restrict__ gri
     extern __shared__ __align__(16) unsigned char smem[];
     float2* buf = reinterpret_cast<float2*>(smem);                        // [ROWS][PITCH]
     float2* Z = buf + R * P::PITCH;                                       // [ROWS][N] sector-0 values
-    const float2* tab = load_tables<N>(a, smem, (size_t)R * P::PITCH * 8 + (size_t)R * N * 8);
+    const float2* tab = load_tables<N>(a, smem, (size_t)R * P::PITCH * 8 + (size_t)R * N * 8, true);
     __syncthreads();
-    const float2 *cin = tab, *cout = tab + 2 * N, *om = tab + 3 * N + L, *filt = tab + 3 * N + 2 * L;
+    const float2 *cin = tab, *cout = tab + 2 * N;
     const int plane = p0 + blockIdx.x / NCB, cb = blockIdx.x % NCB;
     const int fb = plane / N, k = plane % N;
     float2* g = grid + a.grid_off[a.fidx[fb]] + (size_t)k * N;          // g[j1 N^2 + j2]
@@ -490,7 +507,7 @@ lit_inv_cols(BandArgs a, const float2* __restrict__ ws, float2* __restrict__ gri
             buf[cc * P::PITCH + P::pad(mi)] = v;
         }
         __syncthreads();
-        conv_rows<N>(buf, filt, om);
+        conv_rows<N>(buf, tab + 3 * N, tab + 3 * N + L, tab + 3 * N + 2 * L);
         for (int e = threadIdx.x; e < R * N; e += P::THREADS) {
             const int cc = e / N, j2 = e % N, j1 = cb * R + cc;
             if (j1 >= M || j2 >= M) continue;
@@ -514,8 +531,8 @@ lit_inv_cols(BandArgs a, const float2* __restrict__ ws, float2* __restrict__ gri
 template <int N>
 static cudaError_t launch_inv_n(const BandArgs& a, const void* ws, void* grid, cudaStream_t st) {
     using P = Cfg<N>;
-    const size_t smem1 = (size_t)P::ROWS * P::PITCH * 8 + (size_t)P::TAB * 8;
-    const size_t smem2 = (size_t)P::ROWS * P::PITCH * 8 + (size_t)P::ROWS * N * 8 + (size_t)P::TAB * 8;
+    const size_t smem1 = (size_t)P::ROWS * P::PITCH * 8 + (size_t)P::TABX * 8;
+    const size_t smem2 = (size_t)P::ROWS * P::PITCH * 8 + (size_t)P::ROWS * N * 8 + (size_t)P::TABX * 8;
     cudaError_t e = cudaFuncSetAttribute(lit_inv_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(lit_inv_cols<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
@@ -542,7 +559,7 @@ template <int N>
 static cudaError_t launch_n(const BandArgs& a, const void* grid, void* ws, cudaStream_t st) {
     using P = Cfg<N>;
     // launch 1: rows (+ raw rows below N = 256) + tables; launch 2: rows + tables
-    const size_t smem2 = (size_t)P::ROWS * P::PITCH * 8 + (size_t)P::TAB * 8, smem1 = P::smem_bytes();
+    const size_t smem2 = (size_t)P::ROWS * P::PITCH * 8 + (size_t)P::TABX * 8, smem1 = P::smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(lit_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(lit_cols<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
     if (e != cudaSuccess) return e;
