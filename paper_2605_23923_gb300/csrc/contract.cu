@@ -320,9 +320,15 @@ template <int N> struct Cfg {
     static constexpr int PASSES = N / NODES;
     static constexpr int RS = N / 2;
     static constexpr bool FF_POLES = N >= 128;                // float-float chains near the poles (synthesis)
+    // The two halves of a warp (h = 0, 1) read pairs {0, 1} and {2, 3}: the step
+    // coefficients of a pair are CS = RS + 1 entries apart and a row of weighted
+    // coefficients is [pairs 0, 1][2 pad][pairs 2, 3][2 pad], so the two halves
+    // never hit the same bank.
+    static constexpr int CS = RS + 1;
+    static constexpr int CROW = NB * BT + 4;                  // complex values per row of l
     static constexpr size_t smem_bytes() {
-        return sizeof(StepCoef<float>) * NB * RS + sizeof(float2) * RS * NB * BT + sizeof(SeedPair) * NB + 16 * NB +
-               (FF_POLES ? sizeof(float2) * NB * RS : 0);
+        return sizeof(StepCoef<float>) * NB * CS + sizeof(float2) * RS * CROW + sizeof(SeedPair) * NB + 16 * NB +
+               (FF_POLES ? sizeof(float2) * NB * CS : 0);
     }
 };
 }  // namespace tr32
@@ -342,11 +348,12 @@ contract_tr32(BandArgs a, int mode, const float2* __restrict__ coeffs, float2* _
     const int bb = blockIdx.y;
     const int L = tl.L;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    StepCoef<float>* coef = reinterpret_cast<StepCoef<float>*>(smem_raw);   // [NB][RS]
-    float2* Csm = reinterpret_cast<float2*>(coef + NB * RS);               // [RS][NB][BT]
-    SeedPair* spair = reinterpret_cast<SeedPair*>(Csm + RS * NB * BT);      // [NB]
+    constexpr int CS = P::CS, CROW = P::CROW;
+    StepCoef<float>* coef = reinterpret_cast<StepCoef<float>*>(smem_raw);   // [NB][CS]
+    float2* Csm = reinterpret_cast<float2*>(coef + NB * CS);               // [RS][CROW]
+    SeedPair* spair = reinterpret_cast<SeedPair*>(Csm + RS * CROW);         // [NB]
     int* rstart = reinterpret_cast<int*>(spair + NB);                       // [NB] first row of each pair
-    float2* coef_lo = reinterpret_cast<float2*>(rstart + NB);               // [NB][RS] (A, C) low parts
+    float2* coef_lo = reinterpret_cast<float2*>(rstart + NB);               // [NB][CS] (A, C) low parts
     const int tid = threadIdx.x;
     constexpr bool ff = FF;
 
@@ -356,10 +363,10 @@ contract_tr32(BandArgs a, int mode, const float2* __restrict__ coeffs, float2* _
         if (J >= tl.mu2[p]) {
             if (ff) {
                 const StepCoefFF c = step_coef_ff(J, tl.n2[p], tl.m2);
-                coef[p * RS + r] = StepCoef<float>{c.A.h, c.C.h, c.bh, c.bl};
-                coef_lo[p * RS + r] = make_float2(c.A.l, c.C.l);
+                coef[p * CS + r] = StepCoef<float>{c.A.h, c.C.h, c.bh, c.bl};
+                coef_lo[p * CS + r] = make_float2(c.A.l, c.C.l);
             } else {
-                coef[p * RS + r] = step_coef<float>(J, tl.n2[p], tl.m2);
+                coef[p * CS + r] = step_coef<float>(J, tl.n2[p], tl.m2);
             }
         }
     }
@@ -374,7 +381,7 @@ contract_tr32(BandArgs a, int mode, const float2* __restrict__ coeffs, float2* _
             v = cmul_ipow(coeffs[a.coeff_off[f] + ci], (tl.m2 - tl.n2[p]) / 2);
             if (mode == 0) v = cscale(v, (float)(J + 1));
         }
-        Csm[(r * NB + p) * BT + b] = v;
+        Csm[r * CROW + p * BT + (p >= 2 ? 2 : 0) + b] = v;
     }
     if (tid < NB) {
         spair[tid] = make_seed_pair(a.lf2, tl.n2[tid], tl.m2);
@@ -385,8 +392,8 @@ contract_tr32(BandArgs a, int mode, const float2* __restrict__ coeffs, float2* _
     const int h = tid & 1, gidx = tid >> 1;
     const int rs0 = rstart[2 * h], rs1 = rstart[2 * h + 1];
     const SeedPair q0 = spair[2 * h], q1 = spair[2 * h + 1];
-    const StepCoef<float>* c0p = coef + (2 * h) * RS;
-    const StepCoef<float>* c1p = coef + (2 * h + 1) * RS;
+    const StepCoef<float>* c0p = coef + (2 * h) * CS;
+    const StepCoef<float>* c1p = coef + (2 * h + 1) * CS;
     // adjoint prefactor: the grid cell over the Haar measure, 1/(2N^2) on the paper's
     // domain, 1/(4N^2) on the full group (psi over 4 pi), 1/(2(N-1)^2) on the printed grid
     const float NC = a.literal ? (float)(N - 1) : (float)N;
@@ -414,7 +421,7 @@ contract_tr32(BandArgs a, int mode, const float2* __restrict__ coeffs, float2* _
 #pragma unroll
                     for (int b = 0; b < BT; ++b) acc[nd][pp][b] = make_float2(0.f, 0.f);
             for (int r = min(rs0, rs1); r < L; ++r) {
-                const float4* crow = reinterpret_cast<const float4*>(Csm + (r * NB + 2 * h) * BT);
+                const float4* crow = reinterpret_cast<const float4*>(Csm + r * CROW + 2 * h * (BT + 1));
 #pragma unroll
                 for (int pp = 0; pp < 2; ++pp) {
                     if (r < (pp ? rs1 : rs0)) continue;
@@ -426,7 +433,7 @@ contract_tr32(BandArgs a, int mode, const float2* __restrict__ coeffs, float2* _
                         cv[2 * b2 + 1] = make_float2(t.z, t.w);
                     }
                     const StepCoef<float> c32 = (pp ? c1p : c0p)[r];
-                    const float2 clo = coef_lo[(2 * h + pp) * RS + r];
+                    const float2 clo = coef_lo[(2 * h + pp) * CS + r];
                     const StepCoefFF cf{{c32.A, clo.x}, {c32.C, clo.y}, c32.bh, c32.bl};
 #pragma unroll
                     for (int nd = 0; nd < 2; ++nd) {
@@ -475,7 +482,7 @@ contract_tr32(BandArgs a, int mode, const float2* __restrict__ coeffs, float2* _
                 for (int b = 0; b < BT; ++b) acc[nd][pp][b] = make_float2(0.f, 0.f);
 
         for (int r = min(rs0, rs1); r < L; ++r) {
-            const float4* crow = reinterpret_cast<const float4*>(Csm + (r * NB + 2 * h) * BT);
+            const float4* crow = reinterpret_cast<const float4*>(Csm + r * CROW + 2 * h * (BT + 1));
 #pragma unroll
             for (int pp = 0; pp < 2; ++pp) {
                 if (r < (pp ? rs1 : rs0)) continue;           // uniform across the CTA

@@ -47,7 +47,9 @@ struct Cfg {
     static constexpr int NH = N / W;
     static constexpr int NA = 2 * NH, NB = NH, IB = NA + NB;
     static constexpr int THREADS = W * (R1 > R2 ? R1 : R2);
-    static constexpr int RP = R1 * (R2 + 1);            // padded transpose buffer of one row
+    // padded transpose buffer of one row (R2 + 1 per R1 block), plus one so that
+    // the B items' columns (one per lane) start in different banks
+    static constexpr int RP = R1 * (R2 + 1) + 1;
     static constexpr size_t smem_bytes() { return (size_t)2 * W * RP * 8 + (size_t)2 * N * 8 + 16; }
     static constexpr int BLOCKS_PER_SM = (N <= 256) ? 2 : 1;
 };
