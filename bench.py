@@ -570,7 +570,7 @@ def main():
         e2e = {"value": whole_job_value(world, B, args.e2e_steps, ems), "unit": UNIT,
                "h2d_bytes_per_step": host_grid.numel() * 8, "d2h_bytes_per_step": host_out.numel() * 8,
                "steps": args.e2e_steps, "median_step_ms": statistics.median(step_ms),
-               "max_step_ms": max(step_ms),
+               "max_step_ms": max(step_ms), "step_ms": [round(t, 1) for t in step_ms],
                "copies_alone": {"h2d_GB/s": host_grid.numel() * 8 / up_ms / 1e6,
                                 "d2h_GB/s": host_out.numel() * 8 / down_ms / 1e6,
                                 "ms_upload_then_download": up_ms + down_ms}}
