@@ -396,22 +396,22 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
             tc_fence_after();
             const uint32_t base = taddr + ((uint32_t)(32 * q) << 16) + (uint32_t)(h0 * 256);
             const uint32_t pstride = big ? 128u : 64u;
-            // After the TMEM load lane l holds row 32q + l (function 16q + l/2, re or im)
-            // for the 4 pairs.  For the stores, lane t takes function 16q + 8h + t/4 and
-            // pair t%4 (h = 0, 1), so 4 adjacent lanes write 4 consecutive n.
+            // After the TMEM load lane l holds row 32q + l (function 16q + l/2; re for
+            // even l, im for odd l) of every pair.  Lanes 2f and 2f + 1 complete their
+            // values with one exchange per pair they write (shfl.xor 1): the even lane
+            // writes the lower pairs of function 16q + l/2, the odd lane the upper ones.
+            const int fbl = bb * BM + 16 * q + (lane >> 1);
+            const bool okl = fbl < a.nfunc;
+            float2* cfl = coeffs + (okl ? a.coeff_off[a.fidx[fbl]] : 0);
+            const bool odd = lane & 1;
             if (big) {
                 // two halves: pairs 0, 1 (columns 0..255) then pairs 2, 3; half 0 is
-                // released as soon as it is drained.  Lane t: function 16q + t/2, pair
-                // 2g + t%2, so 2 adjacent lanes write 2 consecutive n.
-                const int fb2 = bb * BM + 16 * q + (lane >> 1);
-                const bool ok2 = fb2 < a.nfunc;
-                float2* cf2 = coeffs + (ok2 ? a.coeff_off[a.fidx[fb2]] : 0);
-                const int src2 = 2 * (lane >> 1);
+                // released as soon as it is drained.  Lane l writes pair 2g + l % 2.
 #pragma unroll 1
                 for (int g = 0; g < 2; ++g) {
                     const int p2 = 2 * g + (lane & 1);
                     const int n2t = tl.n2[p2], mu2t = tl.mu2[p2];
-                    const bool vt = tl.valid[p2] && ok2;
+                    const bool vt = tl.valid[p2] && okl;
                     const int ipw = (n2t - tl.m2) / 2;
                     for (int cc = 0; cc < nmma; cc += 16) {
                         uint32_t rv[2][16];
@@ -425,13 +425,14 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
                             const int J = tl.j0 + 2 * r;
                             const size_t rowbase =
                                 (size_t)t_rowoff[J < N ? J : N - 1] + (size_t)((tl.m2 + J) / 2) * (J + 1);
-                            const float r0 = __shfl_sync(0xffffffffu, __uint_as_float(rv[0][j]), src2);
-                            const float i0 = __shfl_sync(0xffffffffu, __uint_as_float(rv[0][j]), src2 + 1);
-                            const float r1 = __shfl_sync(0xffffffffu, __uint_as_float(rv[1][j]), src2);
-                            const float i1 = __shfl_sync(0xffffffffu, __uint_as_float(rv[1][j]), src2 + 1);
-                            const float re = (lane & 1) ? r1 : r0, im = (lane & 1) ? i1 : i0;
+                            // even lane: re of pair 2g is its own, im comes from the odd lane;
+                            // odd lane: im of pair 2g + 1 is its own, re comes from the even lane
+                            const float v0 = __uint_as_float(rv[0][j]), v1 = __uint_as_float(rv[1][j]);
+                            const float own = odd ? v1 : v0;
+                            const float x = __shfl_xor_sync(0xffffffffu, odd ? v0 : v1, 1);
+                            const float re = odd ? x : own, im = odd ? own : x;
                             if (r < Lt && vt && J >= mu2t)
-                                __stcs(&cf2[rowbase + (n2t + J) / 2], cmul_ipow(make_float2(re, im), ipw));
+                                __stcs(&cfl[rowbase + (n2t + J) / 2], cmul_ipow(make_float2(re, im), ipw));
                         }
                     }
                     tc_fence_before();
@@ -440,18 +441,11 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
                 }
                 continue;
             }
-            const int pt = lane & 3;
-            float2* cfh[2];
-            bool okh[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int fb = bb * BM + 16 * q + 8 * h + (lane >> 2);
-                okh[h] = fb < a.nfunc;
-                cfh[h] = coeffs + (okh[h] ? a.coeff_off[a.fidx[fb]] : 0);
-            }
-            const int n2t = tl.n2[pt], mu2t = tl.mu2[pt];
-            const bool vt = tl.valid[pt];
-            const int ipw = (n2t - tl.m2) / 2;
+            // lane l writes pairs pa = 2 (l % 2) and pa + 1 of its function
+            const int pa = odd ? 2 : 0;
+            const int n2a = tl.n2[pa], mu2a = tl.mu2[pa], n2b = tl.n2[pa + 1], mu2b = tl.mu2[pa + 1];
+            const bool va = tl.valid[pa] && okl, vb = tl.valid[pa + 1] && okl;
+            const int ipa = (n2a - tl.m2) / 2, ipb = (n2b - tl.m2) / 2;
             for (int cc = 0; cc < nmma; cc += 16) {
                 uint32_t rv[NP][16];
 #pragma unroll
@@ -463,18 +457,26 @@ contract_tc_kernel(BandArgs a, const __grid_constant__ CUtensorMap tmap, float2*
                     const int r = cc + j;
                     const int J = tl.j0 + 2 * r;
                     const size_t rowbase = (size_t)t_rowoff[J < N ? J : N - 1] + (size_t)((tl.m2 + J) / 2) * (J + 1);
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int src = 16 * h + 2 * (lane >> 2);      // lane holding re of my function
-                        float re = 0.f, im = 0.f;
-#pragma unroll
-                        for (int pp = 0; pp < NP; ++pp) {
-                            const float vr = __shfl_sync(0xffffffffu, __uint_as_float(rv[pp][j]), src);
-                            const float vi = __shfl_sync(0xffffffffu, __uint_as_float(rv[pp][j]), src + 1);
-                            if (pp == pt) { re = vr; im = vi; }
-                        }
-                        if (r < Lt && okh[h] && vt && J >= mu2t)
-                            __stcs(&cfh[h][rowbase + (n2t + J) / 2], cmul_ipow(make_float2(re, im), ipw));   // written once
+                    // even lane sends re of pairs 2, 3 and receives im of pairs 0, 1;
+                    // odd lane sends im of pairs 0, 1 and receives re of pairs 2, 3
+                    const float v0 = __uint_as_float(rv[0][j]), v1 = __uint_as_float(rv[1][j]);
+                    const float v2 = __uint_as_float(rv[2][j]), v3 = __uint_as_float(rv[3][j]);
+                    const float x0 = __shfl_xor_sync(0xffffffffu, odd ? v0 : v2, 1);
+                    const float x1 = __shfl_xor_sync(0xffffffffu, odd ? v1 : v3, 1);
+                    const float o0 = odd ? v2 : v0, o1 = odd ? v3 : v1;
+                    const float2 za = odd ? make_float2(x0, o0) : make_float2(o0, x0);
+                    const float2 zb = odd ? make_float2(x1, o1) : make_float2(o1, x1);
+                    // the two pairs are adjacent coefficients: one 16-byte store where the
+                    // address allows it (a store's cost follows the lines it touches, so
+                    // two 8-byte stores of 16 functions each cost about twice one of 16 bytes)
+                    const bool wa = r < Lt && va && J >= mu2a, wb = r < Lt && vb && J >= mu2b;
+                    float2* pz = &cfl[rowbase + (n2a + J) / 2];
+                    const float2 ya = cmul_ipow(za, ipa), yb = cmul_ipow(zb, ipb);
+                    if (wa && wb && ((reinterpret_cast<uintptr_t>(pz) & 15) == 0)) {
+                        __stcs(reinterpret_cast<float4*>(pz), make_float4(ya.x, ya.y, yb.x, yb.y));   // written once
+                    } else {
+                        if (wa) __stcs(pz, ya);
+                        if (wb) __stcs(pz + 1, yb);
                     }
                 }
             }
