@@ -862,6 +862,13 @@ su2_status su2_plan(su2_plan_t* out, const su2_plan_desc* desc) {
         if (full_group && (N < 64 || N > 256)) return SU2_ERR_UNSUPPORTED;
         Ns[f] = N;
     }
+    // the persistent launch: complex64 on the periodic grid, N = 8..128 (decided
+    // here on the host, before any device call; the plan repeats the check below)
+    if (desc->flags & SU2_FLAG_PERSISTENT) {
+        if (desc->dtype != SU2_C64 || full_group || literal) return SU2_ERR_UNSUPPORTED;
+        for (int N : Ns)
+            if (!su2::ragged_supported(N, false)) return SU2_ERR_UNSUPPORTED;
+    }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return SU2_ERR_CUDA;
     if (desc->device < 0 || desc->device >= ndev) return SU2_ERR_INVALID_ARG;

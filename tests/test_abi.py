@@ -75,6 +75,12 @@ def test_plan_validation_on_host(lib):
     # printed grid: complex64 only, and not together with the full-group grid
     assert lib.su2_plan(ctypes.byref(h), ctypes.byref(_desc(N=16, dtype=1, algo=1, flags=0x8))) == 2
     assert lib.su2_plan(ctypes.byref(h), ctypes.byref(_desc(N=64, dtype=0, algo=2, flags=0xC))) == 1
+    # one persistent launch: complex64 on the periodic grid, N = 8..128 (refused before any device call)
+    assert lib.su2_plan(ctypes.byref(h), ctypes.byref(_desc(N=16, dtype=1, algo=1, flags=0x10))) == 2
+    assert lib.su2_plan(ctypes.byref(h), ctypes.byref(_desc(N=256, dtype=0, algo=3, flags=0x10))) == 2
+    assert lib.su2_plan(ctypes.byref(h), ctypes.byref(_desc(N=4, dtype=0, algo=2, flags=0x10))) == 2
+    assert lib.su2_plan(ctypes.byref(h), ctypes.byref(_desc(N=64, dtype=0, algo=2, flags=0x18))) == 2
+    assert lib.su2_plan(ctypes.byref(h), ctypes.byref(_desc(N=64, dtype=0, algo=3, flags=0x14))) == 2
 
 
 def test_null_plan_calls(lib):
@@ -92,3 +98,5 @@ def test_plan_without_gpu_reports_cuda_error(lib):
         pytest.skip("a GPU is present")
     h = ctypes.c_void_p()
     assert lib.su2_plan(ctypes.byref(h), ctypes.byref(_desc())) == 4
+    # a persistent plan that qualifies gets past the host checks to the device
+    assert lib.su2_plan(ctypes.byref(h), ctypes.byref(_desc(N=64, dtype=0, algo=3, flags=0x10))) == 4
