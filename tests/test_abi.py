@@ -100,3 +100,18 @@ def test_plan_without_gpu_reports_cuda_error(lib):
     assert lib.su2_plan(ctypes.byref(h), ctypes.byref(_desc())) == 4
     # a persistent plan that qualifies gets past the host checks to the device
     assert lib.su2_plan(ctypes.byref(h), ctypes.byref(_desc(N=64, dtype=0, algo=3, flags=0x10))) == 4
+
+
+def test_binding_constants_match_the_header():
+    """Flag bits and status codes of the Python binding equal the header's."""
+    with open(os.path.join(ROOT, "include", "su2fft.h")) as fh:
+        text = fh.read()
+    flags = {m.group(1): int(m.group(2), 16) for m in re.finditer(r"#define SU2_(FLAG_[A-Z_]+) (0x[0-9a-fA-F]+)u", text)}
+    assert flags, "no flags found in the header"
+    for name, value in flags.items():
+        assert getattr(_abi, name) == value, name
+    body = re.search(r"typedef enum \{(.*?)\} su2_status;", text, flags=re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    codes = {m.group(1): int(m.group(2)) for m in re.finditer(r"(SU2_[A-Z_]+) = (\d+)", body)}
+    assert codes["SU2_OK"] == 0 and len(codes) >= 7
+    assert {v: k for k, v in codes.items()} == _abi.STATUS_NAMES
